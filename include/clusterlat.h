@@ -1,0 +1,189 @@
+/*
+ * clusterlat.h -- C ABI of the GB300 lattice scalar-field evolution library
+ * (libclusterlat.so).
+ *
+ * The library evolves nf interacting classical scalar fields on a periodic
+ * d-dimensional lattice (d = 1, 2, 3) with the staggered leapfrog of
+ * arXiv:0712.0813 Sec. III: field values f live at integer times t, their time
+ * derivatives v = f' half a step later; each step advances f by dt with v,
+ * evaluates f'' from the new f and advances v by dt.  Sec. II fixes the
+ * problem statement (a model file with the potential and its derivatives, a
+ * parameter set with lattice size, box, time step, couplings and an expansion
+ * switch; outputs computed from the evolving fields); the Abstract fixes the
+ * scope (1D/2D/3D, with or without expansion of the universe).
+ *
+ * Equations (program units; the paper gives none, these are the readings the
+ * library implements):
+ *   lap f(x)   = dx^-2 sum_d [f(x+e_d) + f(x-e_d) - 2 f(x)],  dx = L/N, periodic
+ *   V          = phi^4/4 + sum_i (q_i/2) phi^2 chi_i^2   (field 0 = phi, i>=1 = chi_i)
+ *   f_i''      = lap f_i - dV/df_i + (a''/a) f_i          (conformally rescaled)
+ *   a''        = (-a'^2 + kappa2 (2 G + 3 V)) / a,  kappa2 = (8 pi/3)(phi0/M_pl)^2
+ *   G          = <sum_i sum_d 1/2 ((f_i(x+e_d) - f_i(x))/dx)^2>,  V = <V(f)>
+ *   a'(t+dt/2) from the implicit midpoint a'_new - a'_old = dt(-a'_mid^2/a + Q).
+ *   Start-up: a(0) = 1, a'(0) = kappa sqrt(K + G + V) with K = <sum 1/2 u^2>,
+ *   f'(0) = u + a'(0) f, then half steps for v and a'.
+ *
+ * Memory: every array argument is a HOST pointer owned by the caller; the
+ * library copies in and out and never keeps a caller pointer.  Host arrays are
+ * float64 in the layout [field][z][y][x] (x fastest; 2D [field][y][x], 1D
+ * [field][x]): nf * N^d contiguous doubles.  Device state is owned by the
+ * handle and lives in HBM until ce_free.
+ *
+ * Errors: every int-returning call returns CE_OK (0) or a negative CE_E* code
+ * and sets a thread-local message readable with ce_last_error().  Invalid
+ * arguments never touch the GPU.  Device-side failures (non-finite energies,
+ * a negative discriminant in the a' update) are latched in a device status
+ * word and reported by the next synchronising call.
+ *
+ * Threading: a handle is not thread-safe; separate handles are independent.
+ * Work is issued asynchronously on the handle's stream.
+ */
+#ifndef CLUSTERLAT_H
+#define CLUSTERLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define CE_OK          0
+#define CE_EINVAL     -1  /* bad argument or configuration                 */
+#define CE_ENOMEM     -2  /* device or host allocation failed              */
+#define CE_ECUDA      -3  /* a CUDA runtime call failed (no device, ...)   */
+#define CE_ETIMEOUT   -4  /* a bounded device wait gave up                 */
+#define CE_ENONFINITE -5  /* NaN/Inf in the global sums or a' update       */
+#define CE_ESTATE     -6  /* call out of order (e.g. step before set_fields) */
+
+/* ---- precision ------------------------------------------------------- */
+#define CE_F64 0          /* fields, velocities and arithmetic in FP64       */
+#define CE_F32 1          /* fields and velocities in FP32; global sums and
+                             a, a', a'' in FP64                              */
+
+/* ---- velocity conventions for ce_set_fields / ce_get_fields ----------- */
+#define CE_VEL_SYNC      0  /* v = u(t) = f'(t) - (a'/a) f(t), synchronised
+                               with f (equals f' without expansion)          */
+#define CE_VEL_STAGGERED 1  /* v = f'(t + dt/2), the leapfrog's own velocity;
+                               with ce_scalars_t this is a complete state    */
+
+/* ---- kernel selection (ce_config.kernel) ------------------------------ */
+#define CE_KERNEL_AUTO    0 /* z-sweep kernel where it applies, else generic  */
+#define CE_KERNEL_GENERIC 1 /* one thread per site, any d and N              */
+#define CE_KERNEL_SWEEP   2 /* 3D z-sweep kernel (CE_EINVAL if it does not apply) */
+
+/* ---- config flags ---------------------------------------------------- */
+#define CE_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt < 2/omega_max check       */
+
+/* Device allocator hooks (optional).  alloc returns a device pointer of at
+ * least `bytes` (256-byte aligned) usable on `stream`, or NULL; release
+ * returns it.  Both NULL: the library uses cudaMalloc/cudaFree. */
+typedef void* (*ce_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ce_release_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+  int dims;              /* 1, 2 or 3 (Abstract: 1D/2D/3D)                     */
+  int64_t N;             /* sites per side, 3 <= N, N^dims <= 2^34            */
+  double L;              /* box side (> 0)                                    */
+  double dt;             /* time step (> 0); rejected above 2/omega_max unless
+                            CE_FLAG_ALLOW_UNSTABLE_DT                          */
+  int nfields;           /* 1..4: field 0 = phi, 1.. = chi_i                  */
+  double q[3];           /* couplings q_i of chi_i (>= 0)                     */
+  int expansion;         /* 0: a == 1; 1: self-consistent a(t) (Abstract)     */
+  double phi0_over_mpl;  /* gravity coupling, kappa2 = 8 pi/3 (phi0/M_pl)^2;
+                            <= 0 selects the default 0.342                    */
+  double phi0;           /* homogeneous phi used only in the dt check (<= 0: 1) */
+  int precision;         /* CE_F64 or CE_F32                                  */
+  int kernel;            /* CE_KERNEL_*                                       */
+  int flags;             /* CE_FLAG_*                                         */
+  void* stream;          /* cudaStream_t to issue work on; NULL = own stream  */
+  ce_alloc_fn alloc;     /* optional device allocator                         */
+  ce_release_fn release;
+  void* alloc_ctx;
+} ce_config;
+
+/* Scale-factor state that, with f(t) and f'(t+dt/2), makes a complete
+ * leapfrog state (checkpoint / resume, Sec. II grid images). */
+typedef struct {
+  double a;              /* a(t)                                              */
+  double ap_half;        /* a'(t + dt/2)                                      */
+  double app;            /* a''(t)                                            */
+  double t;              /* program time                                      */
+  int64_t step;          /* full steps taken since the start-up               */
+} ce_scalars_t;
+
+/* Outputs at integer time t (Sec. II outputs; definitions are readings). */
+typedef struct {
+  double K[4];           /* <1/2 u_i^2>, u synchronised (CE_VEL_SYNC)          */
+  double G[4];           /* gradient energy of field i                        */
+  double V;              /* <V(f)>                                            */
+  double E;              /* sum K + sum G + V                                 */
+  double a;              /* a(t)                                              */
+  double ap;             /* a'(t) = a'(t+dt/2) - dt/2 a''(t)                  */
+  double t;
+  double friedmann_resid;/* |a'^2/kappa2 - E| / E (0 without expansion)       */
+  int64_t step;
+} ce_energy_t;
+
+typedef struct ce_sim ce_sim;
+
+/* Create a simulation handle and allocate its device state (f twice for the
+ * ping-pong of the fused step, the velocity state twice, small scratch).
+ * cfg is read, not kept (stream and allocator hooks are kept).  *out receives
+ * the handle.  Errors: CE_EINVAL (bad config, NULL pointers), CE_ENOMEM,
+ * CE_ECUDA (no device / CUDA failure). */
+int ce_create(const ce_config* cfg, ce_sim** out);
+
+/* Load a state.  f, v: host float64, nf * N^dims each, layout above.
+ *  mode CE_VEL_SYNC:      v = u(0); runs the start-up (a=1, a'(0) from the
+ *                         Friedmann equation, half kick); sc must be NULL.
+ *  mode CE_VEL_STAGGERED: f = f(t), v = f'(t+dt/2) and *sc the matching scalars;
+ *                         restores a state saved by ce_get_fields exactly.
+ * In CE_F32 the values are rounded to float32.  Synchronises.
+ * Errors: CE_EINVAL, CE_ECUDA, CE_ENONFINITE (no real a'(0)). */
+int ce_set_fields(ce_sim* sim, const double* f, const double* v, int mode,
+                  const ce_scalars_t* sc);
+
+/* Advance n >= 0 full steps (Sec. III staggered leapfrog).  Asynchronous on the
+ * handle's stream; device-side failures surface at the next synchronising
+ * call.  Errors: CE_EINVAL (n < 0), CE_ESTATE (no fields set), CE_ECUDA. */
+int ce_step(ce_sim* sim, int64_t n);
+
+/* Block until the handle's stream is idle and report any latched device
+ * error (CE_ENONFINITE). */
+int ce_synchronize(ce_sim* sim);
+
+/* Per-field mean <f_i> and population variance <(f_i - <f_i>)^2> at the
+ * current integer time, FP64 sums.  mean, var: host arrays of nf doubles.
+ * Synchronises. */
+int ce_means_variances(ce_sim* sim, double* mean, double* var);
+
+/* Energies and scale factor at the current integer time.  Synchronises. */
+int ce_energy(ce_sim* sim, ce_energy_t* out);
+
+/* Copy the state out.  f, v: host float64 arrays of nf * N^dims.
+ *  mode CE_VEL_SYNC:      v = u(t) (synchronised); sc may be NULL.
+ *  mode CE_VEL_STAGGERED: v = f'(t+dt/2); *sc (required) receives the scalars.
+ * Synchronises. */
+int ce_get_fields(ce_sim* sim, double* f, double* v, int mode, ce_scalars_t* sc);
+
+/* Release the handle and its device memory.  NULL-safe. */
+void ce_free(ce_sim* sim);
+
+/* Thread-local description of the last error ("" if none). */
+const char* ce_last_error(void);
+
+/* Bytes of device memory the handle holds (state + scratch). */
+int64_t ce_device_bytes(const ce_sim* sim);
+
+/* Which kernel ce_step launches: CE_KERNEL_GENERIC or CE_KERNEL_SWEEP. */
+int ce_kernel_in_use(const ce_sim* sim);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int ce_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
