@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the lattice leapfrog (one JSON line on rank 0).
+
+Workload (default): 3D 256^3 periodic lattice, 2 fields phi, chi with
+V = phi^4/4 + (q/2) phi^2 chi^2, q = 1.2, L = 20, dt = 0.02, expansion on,
+seeded Gaussian-random-field initial conditions (paper_0712_0813_gb300.icgen),
+fields and velocities in FP32 with FP64 global sums and scale factor.
+A "step" is one leapfrog step of the whole lattice (drift, Laplacian, model
+force, kick, global sums, scale-factor update).
+
+Metric: Gsite-updates/s = sites * steps / seconds / 1e9 (one site update
+advances all fields at one site by one step).  The state (537 MB) is larger
+than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (serial FP64 C, test infrastructure) on
+the host cores, each step on a bounded sub-lattice of the same model.
+Multi-GPU: replicas only (independent lattices per rank, no data-path
+collective); launched with torchrun, rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="3d_256cube_2field_expanding", dims=3, N=256, L=20.0, dt=0.02, nf=2,
+                q=(1.2,), expansion=True, phi0=1.0, seed=1)
+METRIC = "Gsite-updates/s"
+STEP_SOURCES = ("ce_sweep3d.cu", "ce_device.cuh", "ce_internal.h")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for name in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_0712_0813_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel_name: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (same hash); else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.md")
+    if not os.path.exists(path):
+        return None
+    pat = re.compile(rf"^traffic\s+{re.escape(kernel_name)}\s+{precision}\s+src=(\w+)\s+bytes_per_launch=(\d+)")
+    cur = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            m = pat.match(line.strip())
+            if m and m.group(1) == cur:
+                return int(m.group(2))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.out = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        if not self.out:
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.out:
+            parts = [p.strip() for p in ln.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, p in zip(names, parts[3:]):
+                if p.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(rank: int):
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    w = WORKLOAD
+    return lattice_ics(w["dims"], w["N"], w["L"], w["nf"], phi0=w["phi0"], q=w["q"], seed=w["seed"] + rank)
+
+
+def sim_config(precision: str, stream):
+    w = WORKLOAD
+    return dict(dims=w["dims"], N=w["N"], L=w["L"], dt=w["dt"], nfields=w["nf"], q=w["q"],
+                expansion=w["expansion"], phi0=w["phi0"], precision=precision, stream=stream)
+
+
+def time_device_steps(capi, torch, f0, u0, precision, steps, warmup, barrier, sampler_gpu=None):
+    """Device-resident timing: CUDA events on the library's stream around `steps` launches."""
+    stream = torch.cuda.Stream()
+    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream))
+    sim.set_fields(f0, u0)
+    sim.step(warmup)
+    sim.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = None
+    barrier()
+    torch.cuda.synchronize()
+    if sampler_gpu is not None:
+        cs = ClockSampler(sampler_gpu)
+        cs.__enter__()
+        time.sleep(0.25)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler_gpu is not None:
+        cs.__exit__(None, None, None)
+        clocks = cs.summary()
+    barrier()
+    sim.synchronize()  # surfaces any latched device error
+    ms = e0.elapsed_time(e1)
+    kernel = {1: "generic", 2: "sweep"}[sim.kernel]
+    sim.close()
+    return ms, kernel, clocks
+
+
+def time_e2e(capi, torch, f0, u0, precision, steps):
+    """End to end through the public API with pinned host buffers: upload of the
+    initial state, start-up, `steps` steps, download of the final state."""
+    nf, S = f0.shape
+    pin_f = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
+    pin_u = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
+    out_f = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
+    out_v = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
+    pin_f[:] = f0.reshape(-1)
+    pin_u[:] = u0.reshape(-1)
+    stream = torch.cuda.Stream()
+    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream))
+    sim.set_fields(pin_f, pin_u)  # warm (first-touch, module load)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_fields(pin_f, pin_u)
+    sim.step(steps)
+    capi.ce_get_fields(sim.handle, nf, S, capi.CE_VEL_SYNC, out=(out_f, out_v))
+    t1 = time.perf_counter()
+    sim.close()
+    nbytes = 2 * nf * S * 8
+    return t1 - t0, nbytes
+
+
+def cpu_oracle_rate(f0, u0, target_s: float, N_sample: int | None = None):
+    """Sites/s of the CPU oracle (serial, 1 thread) on the bench model."""
+    import oracle
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    w = WORKLOAD
+    if N_sample is None or N_sample == w["N"]:
+        N = w["N"]
+        fs, us = f0, u0
+    else:
+        N = N_sample
+        fs, us = lattice_ics(w["dims"], N, w["L"], w["nf"], phi0=w["phi0"], q=w["q"], seed=w["seed"])
+    p = oracle.Params(dims=w["dims"], N=N, L=w["L"], dt=w["dt"], nf=w["nf"], q=w["q"], expansion=w["expansion"])
+    st = oracle.init(p, fs, us)
+    t0 = time.perf_counter()
+    oracle.step(st, 1)
+    one = time.perf_counter() - t0
+    k = max(1, int(target_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    oracle.step(st, k)
+    el = time.perf_counter() - t0
+    return (N ** w["dims"]) * (k + 1) / (el + one), k + 1, N, el + one
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on this host's cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    oracle.build()
+    w = WORKLOAD
+    # size each step's sub-lattice so that warmup + steps stay within ~150 s
+    probe_N = 32
+    rate, _, _, _ = cpu_oracle_rate(None, None, 0.5, N_sample=probe_N)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    N = 8
+    for cand in (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256):
+        if cand ** 3 / rate <= budget:
+            N = cand
+    fs, us = lattice_ics(w["dims"], N, w["L"], w["nf"], phi0=w["phi0"], q=w["q"], seed=w["seed"])
+    p = oracle.Params(dims=w["dims"], N=N, L=w["L"], dt=w["dt"], nf=w["nf"], q=w["q"], expansion=w["expansion"])
+    st = oracle.init(p, fs, us)
+    oracle.step(st, args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(st, args.steps)
+    el = time.perf_counter() - t0
+    value = (N ** 3) * args.steps / el / 1e9
+    sample = f"each step = one oracle step of a {N}^3 sub-lattice of the same model (bounded sample of the 256^3 workload)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "sample_N": N, "precision": "f64",
+                                        "expansion": True, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}), flush=True)
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_0712_0813_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_0712_0813_gb300 import capi
+
+    w = WORKLOAD
+    S = w["N"] ** w["dims"]
+    f0, u0 = make_inputs(rank)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+
+    ms, kernel, clocks = time_device_steps(capi, torch, f0, u0, args.precision, args.steps, args.warmup,
+                                           barrier, sampler_gpu=gpu_index if rank == 0 else None)
+    ms = max_over_ranks(ms)
+    secs = ms / 1e3
+    value = ws * S * args.steps / secs / 1e9
+
+    # plain FP64 path on the same lattice (context for the FP32/FP64 ratio)
+    ms64, kernel64, _ = time_device_steps(capi, torch, f0, u0, "f64", args.fp64_steps, args.warmup, barrier)
+    ms64 = max_over_ranks(ms64)
+    value64 = ws * S * args.fp64_steps / (ms64 / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        t_e2e, nbytes = time_e2e(capi, torch, f0, u0, args.precision, args.steps)
+        t_e2e = max_over_ranks(t_e2e)
+        e2e = {"value": ws * S * args.steps / t_e2e / 1e9, "unit": METRIC,
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "job": f"set_fields(host f,u) + {args.steps} steps + get_fields(host f,u), pinned host buffers"}
+
+    hbm_peak, peak_kind = peaks()
+    esize = 4 if args.precision == "f32" else 8
+    alg_bytes = 4 * esize * w["nf"] * S          # read f, w; write f, w per field and site
+    launch_s = secs / args.steps                  # one step kernel per step
+    achieved = alg_bytes / launch_s / 1e9
+    kname = "k_step_sweep" if kernel == "sweep" else "k_step_generic"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": ncu_traffic(kname, args.precision),
+                "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, k, Ns, el = cpu_oracle_rate(f0, u0, args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"{k} oracle steps of the full {Ns}^3 lattice ({el:.1f} s, serial FP64 C)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": w["name"], "N": w["N"], "fields": w["nf"], "expansion": w["expansion"],
+                       "dt": w["dt"], "L": w["L"], "precision": args.precision,
+                       "storage": "fields+velocities " + args.precision + ", global sums and a(t) f64",
+                       "kernel": kernel, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "state 4x larger than L2; no flush needed"},
+            "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                           "kernel": kernel64, "f32_over_f64": value / value64},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

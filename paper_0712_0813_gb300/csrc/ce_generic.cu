@@ -1,0 +1,431 @@
+// ce_generic.cu -- the generic fused step kernel (any dimension, any N >= 3,
+// one thread per site), the diagnostics pass, the start-up scalar kernel and
+// the host<->device conversion kernels of libclusterlat.
+//
+// The fused step (arXiv:0712.0813 Sec. III staggered leapfrog) per site x and
+// field i, with state (f_n, w_n) and v_{n+1/2} = w_n + c_n f_n:
+//   v      = w + c f                        expansion kick of the previous step
+//   g      = f + dt_drift v                 drift: g = f_{n+1}, also at the 2d neighbours
+//   F0     = lap g - dV/df(g)               nearest-neighbour Laplacian (periodic wrap
+//                                           by index arithmetic), model force
+//   w_out  = v + dt_kick F0,  f_out = g     kick without the (a''/a) f term
+// plus block partial sums of sum_d (g(x+e_d) - g(x))^2 and V(g) for the scale
+// factor.  f is ping-ponged because neighbours of the old f are still being read
+// while the new one is written; the velocity state is ping-ponged for the same
+// reason (its neighbours are read to form g there).
+#include <cstdint>
+
+#include "ce_device.cuh"
+#include "ce_internal.h"
+
+namespace ce {
+
+int generic_blocks(int64_t S) {
+  int64_t want = (S + kGenericThreads - 1) / kGenericThreads;
+  const int64_t cap = 152 * 8;
+  return (int)(want < cap ? want : cap);
+}
+
+template <typename T, int NF, int DIMS>
+__global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs<T> p) {
+  const T c = (T)p.sc_in->c;
+  const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
+  const int64_t N = p.N, S = p.S, NN = N * N;
+  T q[3] = {p.q[0], p.q[1], p.q[2]};
+  double grad2 = 0.0, pot = 0.0;   // flushed from the T partials every 16 sites
+  T g2loc = T(0), vloc = T(0);
+  int since_flush = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += stride) {
+    const int64_t x = s % N;
+    const int64_t r = s / N;
+    int64_t nb[2 * DIMS];
+    nb[0] = (x == N - 1) ? s - (N - 1) : s + 1;
+    nb[1] = (x == 0) ? s + (N - 1) : s - 1;
+    if (DIMS >= 2) {
+      const int64_t y = (DIMS == 2) ? r : r % N;
+      nb[2] = (y == N - 1) ? s - (N - 1) * N : s + N;
+      nb[3] = (y == 0) ? s + (N - 1) * N : s - N;
+    }
+    if (DIMS >= 3) {
+      const int64_t z = r / N;
+      nb[4] = (z == N - 1) ? s - (N - 1) * NN : s + NN;
+      nb[5] = (z == 0) ? s + (N - 1) * NN : s - NN;
+    }
+    T g[NF], v[NF], lap[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      const T* fi = p.f_in[i];
+      const T* wi = p.w_in[i];
+      const T f0 = fi[s];
+      v[i] = fmaT(c, f0, wi[s]);
+      g[i] = fmaT(dd, v[i], f0);
+      T acc = T(0);
+#pragma unroll
+      for (int d = 0; d < DIMS; ++d) {
+        const T fp = fi[nb[2 * d]], fm = fi[nb[2 * d + 1]];
+        const T gp = fmaT(dd, fmaT(c, fp, wi[nb[2 * d]]), fp);
+        const T gm = fmaT(dd, fmaT(c, fm, wi[nb[2 * d + 1]]), fm);
+        acc += (gp + gm) - T(2) * g[i];
+        const T df = gp - g[i];
+        g2loc = fmaT(df, df, g2loc);
+      }
+      lap[i] = acc * idx2;
+    }
+    T dv[NF], vs;
+    model_dv<T, NF>(g, q, dv, vs);
+    vloc += vs;
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      p.w_out[i][s] = fmaT(kk, lap[i] - dv[i], v[i]);
+      p.f_out[i][s] = g[i];
+    }
+    if (++since_flush == 16) {
+      grad2 += (double)g2loc;
+      pot += (double)vloc;
+      g2loc = T(0);
+      vloc = T(0);
+      since_flush = 0;
+    }
+  }
+  if (p.update_scalars) {
+    grad2 += (double)g2loc;
+    pot += (double)vloc;
+    finish_step_block(p, grad2, pot);
+  }
+}
+
+template <typename T, int NF>
+static cudaError_t launch_generic_nf(const StepArgs<T>& a, int blocks, cudaStream_t st) {
+  switch (a.dims) {
+    case 1: k_step_generic<T, NF, 1><<<blocks, kGenericThreads, 0, st>>>(a); break;
+    case 2: k_step_generic<T, NF, 2><<<blocks, kGenericThreads, 0, st>>>(a); break;
+    default: k_step_generic<T, NF, 3><<<blocks, kGenericThreads, 0, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step_generic(const StepArgs<T>& a, int blocks, cudaStream_t st) {
+  switch (a.nf) {
+    case 1: return launch_generic_nf<T, 1>(a, blocks, st);
+    case 2: return launch_generic_nf<T, 2>(a, blocks, st);
+    case 3: return launch_generic_nf<T, 3>(a, blocks, st);
+    default: return launch_generic_nf<T, 4>(a, blocks, st);
+  }
+}
+template cudaError_t launch_step_generic<float>(const StepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_step_generic<double>(const StepArgs<double>&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Diagnostics: u(t_n), energies and moments in FP64 (on demand, not per step).
+//   v_half = w + c f;  v(t_n) = v_half - dt/2 (lap f - dV/df + s f)
+//   a'(t_n) = a'_{n+1/2} - dt/2 a''_n;  u = v(t_n) - (a'(t_n)/a_n) f
+// With raw_u (start-up input) u is w itself.
+
+template <typename T, int NF, int DIMS>
+__device__ __forceinline__ void site_u(const DiagArgs<T>& p, int64_t s, double (&fv)[NF],
+                                       double (&u)[NF], double (&g2)[NF]) {
+  const int64_t N = p.N, NN = N * N;
+  const int64_t x = s % N, r = s / N;
+  int64_t nb[2 * DIMS];
+  nb[0] = (x == N - 1) ? s - (N - 1) : s + 1;
+  nb[1] = (x == 0) ? s + (N - 1) : s - 1;
+  if (DIMS >= 2) {
+    const int64_t y = (DIMS == 2) ? r : r % N;
+    nb[2] = (y == N - 1) ? s - (N - 1) * N : s + N;
+    nb[3] = (y == 0) ? s + (N - 1) * N : s - N;
+  }
+  if (DIMS >= 3) {
+    const int64_t z = r / N;
+    nb[4] = (z == N - 1) ? s - (N - 1) * NN : s + NN;
+    nb[5] = (z == 0) ? s + (N - 1) * NN : s - NN;
+  }
+  double lap[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    const T* fi = p.f[i];
+    fv[i] = (double)fi[s];
+    double acc = 0.0, gg = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIMS; ++d) {
+      const double fp = (double)fi[nb[2 * d]], fm = (double)fi[nb[2 * d + 1]];
+      acc += (fp + fm) - 2.0 * fv[i];
+      gg += (fp - fv[i]) * (fp - fv[i]);
+    }
+    lap[i] = acc * p.inv_dx2;
+    g2[i] = gg;
+  }
+  if (p.raw_u) {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) u[i] = (double)p.w[i][s];
+    return;
+  }
+  const DevScalars sc = *p.sc;
+  double dv[NF], vs;
+  double q[3] = {p.q[0], p.q[1], p.q[2]};
+  model_dv<double, NF>(fv, q, dv, vs);
+  const double h = p.expansion ? (sc.ap - 0.5 * p.dt * sc.app) / sc.a : 0.0;
+  const double sterm = p.expansion ? sc.s : 0.0;
+  const T cT = (T)sc.c;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    const T vh = fmaT(cT, p.f[i][s], p.w[i][s]);
+    const double vsync = (double)vh - 0.5 * p.dt * (lap[i] - dv[i] + sterm * fv[i]);
+    u[i] = vsync - h * fv[i];
+  }
+}
+
+// partial layout per block: [K_i (NF)][G_i (NF)][V][sum(f_i - f_i(0)) (NF)][sum (f_i - f_i(0))^2 (NF)]
+template <typename T, int NF, int DIMS>
+__global__ void __launch_bounds__(256) k_diag(const DiagArgs<T> p) {
+  constexpr int NV = 4 * NF + 1;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  double shift[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) shift[i] = (double)p.f[i][0];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.S; s += stride) {
+    double fv[NF], u[NF], g2[NF];
+    site_u<T, NF, DIMS>(p, s, fv, u, g2);
+    double dv[NF], vs;
+    double q[3] = {p.q[0], p.q[1], p.q[2]};
+    model_dv<double, NF>(fv, q, dv, vs);
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      acc[i] += 0.5 * u[i] * u[i];
+      acc[NF + i] += g2[i];
+      const double df = fv[i] - shift[i];
+      acc[2 * NF + 1 + i] += df;
+      acc[3 * NF + 1 + i] += df * df;
+    }
+    acc[2 * NF] += vs;
+  }
+  __shared__ double red[8][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    p.partials[(int64_t)blockIdx.x * NV + threadIdx.x] = t;
+  }
+}
+
+// One block: combine the diag partials in block order and derive the outputs.
+template <int NF>
+__global__ void k_diag_finalize(const double* partials, int blocks, DevAux* aux, int64_t S,
+                                double half_inv_dx2, double dt, double kappa2, int expansion,
+                                const DevScalars* sc) {
+  constexpr int NV = 4 * NF + 1;
+  __shared__ double tot[NV];
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int b = 0; b < blocks; ++b) t += partials[(int64_t)b * NV + threadIdx.x];
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* r = aux->result;
+  for (int k = 0; k < kResultLen; ++k) r[k] = 0.0;
+  const double invS = 1.0 / (double)S;
+  double K = 0.0, G = 0.0;
+  for (int i = 0; i < NF; ++i) {
+    r[R_K + i] = tot[i] * invS;
+    r[R_G + i] = tot[NF + i] * half_inv_dx2 * invS;
+    K += r[R_K + i];
+    G += r[R_G + i];
+  }
+  r[R_V] = tot[2 * NF] * invS;
+  r[R_KTOT] = K;
+  r[R_GTOT] = G;
+  const double E = K + G + r[R_V];
+  r[R_E] = E;
+  const DevScalars s = *sc;
+  const double ap_t = expansion ? s.ap - 0.5 * dt * s.app : 0.0;
+  r[R_A] = expansion ? s.a : 1.0;
+  r[R_AP] = ap_t;
+  r[R_RESID] = expansion ? fabs(ap_t * ap_t / kappa2 - E) / E : 0.0;
+  for (int i = 0; i < NF; ++i) {
+    const double m1 = tot[2 * NF + 1 + i] * invS;   // <f - shift>
+    const double m2 = tot[3 * NF + 1 + i] * invS;   // <(f - shift)^2>
+    r[R_MEAN + i] = m1;                             // k_mean_shift adds the shift back
+    r[R_VAR + i] = m2 - m1 * m1;
+  }
+  if (!isfinite(E)) atomicCAS(&aux->status, CE_OK, CE_ENONFINITE);
+}
+
+template <typename T, int NF>
+__global__ void k_mean_shift(DevAux* aux, const T* f0, const T* f1, const T* f2, const T* f3) {
+  const T* fs[4] = {f0, f1, f2, f3};
+  for (int i = 0; i < NF; ++i) aux->result[R_MEAN + i] += (double)fs[i][0];
+}
+
+template <typename T, int NF, int DIMS>
+__global__ void __launch_bounds__(256) k_sync_u_range(const DiagArgs<T> p) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.count; k += stride) {
+    const int64_t s = p.s0 + k;
+    double fv[NF], u[NF], g2[NF];
+    site_u<T, NF, DIMS>(p, s, fv, u, g2);
+#pragma unroll
+    for (int i = 0; i < NF; ++i) p.u_out[(int64_t)i * p.count + k] = u[i];
+  }
+}
+
+template <typename T, int NF>
+static cudaError_t launch_diag_nf(const DiagArgs<T>& a, int blocks, cudaStream_t st) {
+  switch (a.dims) {
+    case 1: k_diag<T, NF, 1><<<blocks, 256, 0, st>>>(a); break;
+    case 2: k_diag<T, NF, 2><<<blocks, 256, 0, st>>>(a); break;
+    default: k_diag<T, NF, 3><<<blocks, 256, 0, st>>>(a); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double dx2inv = a.inv_dx2;
+  k_diag_finalize<NF><<<1, 64, 0, st>>>(a.partials, blocks, a.aux, a.S, 0.5 * dx2inv, a.dt, a.kappa2,
+                                         a.expansion, a.sc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_mean_shift<T, NF><<<1, 1, 0, st>>>(a.aux, a.f[0], a.f[NF > 1 ? 1 : 0], a.f[NF > 2 ? 2 : 0],
+                                       a.f[NF > 3 ? 3 : 0]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag(const DiagArgs<T>& a, int blocks, cudaStream_t st) {
+  switch (a.nf) {
+    case 1: return launch_diag_nf<T, 1>(a, blocks, st);
+    case 2: return launch_diag_nf<T, 2>(a, blocks, st);
+    case 3: return launch_diag_nf<T, 3>(a, blocks, st);
+    default: return launch_diag_nf<T, 4>(a, blocks, st);
+  }
+}
+template cudaError_t launch_diag<float>(const DiagArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_diag<double>(const DiagArgs<double>&, int, cudaStream_t);
+
+template <typename T, int NF>
+static cudaError_t launch_sync_nf(const DiagArgs<T>& a, cudaStream_t st) {
+  int64_t want = (a.count + 255) / 256;
+  int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  if (blocks < 1) blocks = 1;
+  switch (a.dims) {
+    case 1: k_sync_u_range<T, NF, 1><<<blocks, 256, 0, st>>>(a); break;
+    case 2: k_sync_u_range<T, NF, 2><<<blocks, 256, 0, st>>>(a); break;
+    default: k_sync_u_range<T, NF, 3><<<blocks, 256, 0, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sync_u_range(const DiagArgs<T>& a, cudaStream_t st) {
+  switch (a.nf) {
+    case 1: return launch_sync_nf<T, 1>(a, st);
+    case 2: return launch_sync_nf<T, 2>(a, st);
+    case 3: return launch_sync_nf<T, 3>(a, st);
+    default: return launch_sync_nf<T, 4>(a, st);
+  }
+}
+template cudaError_t launch_sync_u_range<float>(const DiagArgs<float>&, cudaStream_t);
+template cudaError_t launch_sync_u_range<double>(const DiagArgs<double>&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Start-up scalars (reading c-6), one thread, after a raw-u diagnostics pass
+// over (f(0), u(0)):  a = 1, a'(0) = sqrt(kappa2 (K + G + V)),
+//   a''(0) = (-a'(0)^2 + kappa2 (2G + 3V)) / a.
+// slot[cur]   feeds the half-kick launch: c = a'(0)/a turns u into f'(0).
+// slot[cur^1] is the state after it: a'(dt/2) = a'(0) + dt/2 a''(0) and
+//             c = dt/2 a''(0)/a, the expansion half of the half kick.
+__global__ void k_init_scalars(DevAux* aux, int cur, int expansion, double dt, double kappa2) {
+  const double* r = aux->result;
+  const double K = r[R_KTOT], G = r[R_GTOT], V = r[R_V];
+  double ap0 = 0.0, app0 = 0.0;
+  const double a = 1.0;
+  if (expansion) {
+    const double rho = K + G + V;
+    if (!(rho >= 0.0) || !isfinite(rho)) atomicCAS(&aux->status, CE_OK, CE_ENONFINITE);
+    ap0 = sqrt(kappa2 * rho);
+    app0 = (-ap0 * ap0 + kappa2 * (2.0 * G + 3.0 * V)) / a;
+  }
+  DevScalars s0;
+  s0.a = a; s0.ap = ap0; s0.app = 0.0; s0.s = 0.0; s0.c = ap0 / a; s0.G = G; s0.V = V; s0.pad = 0.0;
+  DevScalars s1;
+  s1.a = a;
+  s1.ap = ap0 + 0.5 * dt * app0;
+  s1.app = app0;
+  s1.s = app0 / a;
+  s1.c = 0.5 * dt * s1.s;
+  s1.G = G; s1.V = V; s1.pad = 0.0;
+  aux->slot[cur] = s0;
+  aux->slot[cur ^ 1] = s1;
+}
+
+cudaError_t launch_init_scalars(DevAux* aux, int cur, int expansion, double dt, double kappa2,
+                                cudaStream_t st) {
+  k_init_scalars<<<1, 1, 0, st>>>(aux, cur, expansion, dt, kappa2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Conversions between the caller's float64 host layout (staged in HBM) and the
+// storage type.
+
+template <typename T>
+__global__ void k_from_f64(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) dst[k] = (T)src[k];
+}
+
+template <typename T>
+__global__ void k_to_f64(const T* __restrict__ src, double* __restrict__ dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) dst[k] = (double)src[k];
+}
+
+// f'(t+dt/2) = w + c f, rounded in T exactly as the step kernel forms it.
+template <typename T>
+__global__ void k_vhalf_to_f64(const T* __restrict__ f, const T* __restrict__ w, const DevScalars* sc,
+                               double* __restrict__ dst, int64_t n) {
+  const T c = (T)sc->c;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+    dst[k] = (double)fmaT(c, f[k], w[k]);
+}
+
+static int conv_blocks(int64_t n) {
+  int64_t want = (n + 255) / 256;
+  return (int)(want < 152 * 16 ? (want < 1 ? 1 : want) : 152 * 16);
+}
+
+template <typename T>
+cudaError_t launch_from_f64(const double* src, T* dst, int64_t n, cudaStream_t st) {
+  k_from_f64<T><<<conv_blocks(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_to_f64(const T* src, double* dst, int64_t n, cudaStream_t st) {
+  k_to_f64<T><<<conv_blocks(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_vhalf_to_f64(const T* f, const T* w, const DevScalars* sc, double* dst, int64_t n,
+                                cudaStream_t st) {
+  k_vhalf_to_f64<T><<<conv_blocks(n), 256, 0, st>>>(f, w, sc, dst, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_from_f64<float>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_from_f64<double>(const double*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_to_f64<float>(const float*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_to_f64<double>(const double*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_vhalf_to_f64<float>(const float*, const float*, const DevScalars*, double*,
+                                                int64_t, cudaStream_t);
+template cudaError_t launch_vhalf_to_f64<double>(const double*, const double*, const DevScalars*,
+                                                 double*, int64_t, cudaStream_t);
+
+}  // namespace ce

@@ -1,0 +1,135 @@
+// ce_internal.h -- structures shared by the host side of the C ABI and the
+// kernels of libclusterlat.  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "clusterlat.h"
+
+namespace ce {
+
+// Scale-factor state belonging to one integer time t_n.  Two slots alternate
+// between step launches (launch k reads slot k%2 and writes slot (k+1)%2), so a
+// launch never overwrites what its own blocks are still reading.
+//
+// The velocity state kept in HBM is w with  f'(t_n + dt/2) = w + c f(t_n).  The
+// fused step kernel cannot add the expansion term (a''/a) f of its own kick,
+// because a'' needs the global sums of the f it is writing; that term is folded
+// in by the next launch through c = dt a''/a (and c = 0 after a restore).
+struct DevScalars {
+  double a;    // a(t_n)
+  double ap;   // a'(t_n + dt/2)
+  double app;  // a''(t_n)
+  double s;    // a''(t_n) / a(t_n)
+  double c;    // coefficient of f in the velocity reconstruction above
+  double G;    // mean gradient energy of f(t_n) (when computed by a step)
+  double V;    // mean potential energy of f(t_n)
+  double pad;
+};
+
+constexpr int kResultLen = 64;
+
+// Result layout of the diagnostics pass (doubles).
+enum ResultIndex : int {
+  R_K = 0,       // 4: <1/2 u_i^2>
+  R_G = 4,       // 4: gradient energy per field
+  R_V = 8,
+  R_E = 9,
+  R_A = 10,
+  R_AP = 11,     // a'(t) at integer time
+  R_RESID = 12,
+  R_MEAN = 13,   // 4
+  R_VAR = 17,    // 4
+  R_KTOT = 21,
+  R_GTOT = 22,
+};
+
+struct DevAux {
+  DevScalars slot[2];
+  int status;              // CE_OK or the first device-side error code
+  unsigned int counter;    // last-block-done counter of the step reduction
+  unsigned int counter_diag;
+  int pad;
+  double result[kResultLen];
+};
+
+// Arguments of one step launch.  T is the storage/arithmetic type of fields
+// and velocities; the global sums and scalars are always double.
+template <typename T>
+struct StepArgs {
+  const T* f_in[4];
+  const T* w_in[4];
+  T* f_out[4];
+  T* w_out[4];
+  int64_t N;
+  int64_t S;
+  int dims;
+  int nf;
+  T inv_dx2;
+  T dt_drift;      // dt for a step, 0 for the start-up half kick
+  T dt_kick;       // dt for a step, dt/2 for the start-up half kick
+  T q[3];
+  double dt;
+  double kappa2;
+  double inv_S;
+  double half_inv_dx2;
+  int update_scalars;   // 1: reduce G, V and advance a, a', a'' in the last block
+  const DevScalars* sc_in;
+  DevScalars* sc_out;
+  double* partials;     // >= 2 * number of blocks
+  unsigned int* counter;
+  int* status;
+};
+
+// Arguments of the diagnostics pass (energies, moments, synchronised u).
+template <typename T>
+struct DiagArgs {
+  const T* f[4];
+  const T* w[4];
+  int64_t N;
+  int64_t S;
+  int dims;
+  int nf;
+  double inv_dx2;
+  double dt;
+  double q[3];
+  double kappa2;
+  int expansion;
+  int raw_u;            // 1: w holds u itself (start-up input), no correction
+  const DevScalars* sc;
+  double* partials;     // nvals * blocks
+  DevAux* aux;
+  double* u_out;        // sync_u_range only: u of sites [s0, s0 + count)
+  int64_t s0;
+  int64_t count;
+};
+
+// ---- launchers (return cudaError_t of the launch) -------------------------
+template <typename T> cudaError_t launch_step_generic(const StepArgs<T>& a, int blocks, cudaStream_t st);
+template <typename T> cudaError_t launch_diag(const DiagArgs<T>& a, int blocks, cudaStream_t st);
+template <typename T> cudaError_t launch_sync_u_range(const DiagArgs<T>& a, cudaStream_t st);
+cudaError_t launch_init_scalars(DevAux* aux, int cur, int expansion, double dt, double kappa2,
+                                cudaStream_t st);
+template <typename T> cudaError_t launch_from_f64(const double* src, T* dst, int64_t n, cudaStream_t st);
+template <typename T> cudaError_t launch_to_f64(const T* src, double* dst, int64_t n, cudaStream_t st);
+template <typename T> cudaError_t launch_vhalf_to_f64(const T* f, const T* w, const DevScalars* sc,
+                                                      double* dst, int64_t n, cudaStream_t st);
+
+// 3D z-sweep kernel (sm_103a): availability check and launcher.
+struct SweepPlan {
+  int tx, ty, tz;         // tile extents (sites)
+  int gx, gy, gz;         // grid
+  int threads;
+  size_t smem;
+};
+bool sweep_supported(int dims, int64_t N, int nf, int prec);
+SweepPlan sweep_plan(int64_t N, int nf, int prec);
+template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
+                                                    cudaStream_t st);
+
+constexpr int kGenericThreads = 256;
+int generic_blocks(int64_t S);
+constexpr int kDiagBlocksMax = 1216;   // 8 per SM on a 152-SM GB300
+
+}  // namespace ce

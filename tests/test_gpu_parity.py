@@ -1,0 +1,175 @@
+"""CUDA path vs CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64): relative max error max|gpu - ref| / max|ref| per field and
+per velocity array, and |d|/|ref| for scalars, <= 1e-11 after 100 steps.  The
+two sides round differently (FMA contraction, summation order of the global
+sums, the velocity kept as w + c f), each step adding O(1e-16) relative
+error that the dynamics carry forward; 1e-11 leaves about three decades of
+margin over 100 steps of these runs.
+FP32 storage: errors are reported against the FP64 oracle and checked only
+against the 1e-3 statistics bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0712_0813_gb300.icgen import lattice_ics
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+def relmax(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def per_field_err(a, b, nf):
+    a = np.asarray(a).reshape(nf, -1)
+    b = np.asarray(b).reshape(nf, -1)
+    return max(relmax(a[i], b[i]) for i in range(nf))
+
+
+def run_pair(orc, capi, dims, N, L, dt, nf, q, expansion, steps, precision="f64", kernel="auto",
+             seed=1, phi0=1.0, amp=1e-4):
+    f0, u0 = lattice_ics(dims, N, L, nf, phi0=phi0, q=q, seed=seed, amp=amp)
+    p = orc.Params(dims=dims, N=N, L=L, dt=dt, nf=nf, q=tuple(q) if q else (0.0,), expansion=expansion)
+    ref = orc.init(p, f0, u0)
+    orc.step(ref, steps)
+    sim = capi.Simulation(dims=dims, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=expansion,
+                          precision=precision, kernel=kernel, phi0=phi0)
+    sim.set_fields(f0, u0)
+    sim.step(steps)
+    f, v, sc = sim.get_fields(capi.CE_VEL_STAGGERED)
+    return ref, sim, f, v, sc
+
+
+CASES = [
+    # dims, N, L, dt, nf, q, expansion
+    (3, 32, 20.0, 0.05, 2, (1.2,), False),   # the plain 32^3 FP64 case
+    (3, 32, 20.0, 0.05, 2, (1.2,), True),
+    (3, 64, 20.0, 0.02, 2, (1.2,), True),
+    (1, 4096, 20.0, 0.004, 2, (1.2,), True),
+    (2, 256, 20.0, 0.02, 2, (1.2,), True),
+    (3, 3, 2.0, 0.05, 2, (1.2,), True),      # every neighbour wraps
+    (3, 5, 3.0, 0.05, 1, (), True),
+    (3, 37, 20.0, 0.05, 3, (0.8, 5.0), True),  # ragged N
+    (3, 20, 20.0, 0.03, 4, (0.8, 5.0, 40.0), True),
+    (2, 100, 20.0, 0.05, 4, (0.8, 5.0, 40.0), False),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d_N{c[1]}_nf{c[4]}_{'exp' if c[6] else 'flat'}" for c in CASES])
+def test_fp64_parity_100_steps(gpu_capi, orc, case):
+    dims, N, L, dt, nf, q, expansion = case
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, expansion, 100)
+    with sim:
+        assert per_field_err(f, ref.f, nf) <= TOL64
+        assert per_field_err(v, ref.v, nf) <= TOL64
+        assert sc.step == 100 and sc.t == ref.scale.t
+        if expansion:
+            assert abs(sc.a - ref.scale.a) / ref.scale.a <= TOL64
+            assert abs(sc.ap_half - ref.scale.ap) / abs(ref.scale.ap) <= TOL64
+            assert abs(sc.app - ref.scale.app) / abs(ref.scale.app) <= 1e-9
+        else:
+            assert sc.a == 1.0 and sc.ap_half == 0.0
+        en_ref = orc.energy(ref)
+        en = sim.energy()
+        for key in ("V", "E", "a", "ap"):
+            assert en[key] == pytest.approx(en_ref[key], rel=1e-10, abs=1e-14), key
+        np.testing.assert_allclose(en["K"], en_ref["K"], rtol=1e-8, atol=1e-15)
+        np.testing.assert_allclose(en["G"], en_ref["G"], rtol=1e-8, atol=1e-15)
+        if expansion:
+            assert en["friedmann_resid"] == pytest.approx(en_ref["friedmann_resid"], rel=1e-6, abs=1e-12)
+        mean, var = sim.means_variances()
+        mref, vref = orc.means_variances(ref.p, ref.f)
+        np.testing.assert_allclose(mean, mref, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(var, vref, rtol=1e-6, atol=1e-18)
+        fs, us, _ = sim.get_fields(gpu_capi.CE_VEL_SYNC)
+        assert per_field_err(us, orc.sync_u(ref), nf) <= TOL64
+
+
+def test_startup_roundtrip_returns_input_velocity(gpu_capi, orc):
+    f0, u0 = lattice_ics(3, 16, 20.0, 2, q=(1.2,), seed=5)
+    with gpu_capi.Simulation(dims=3, N=16, L=20.0, dt=0.05, nfields=2, q=(1.2,), expansion=True) as sim:
+        sim.set_fields(f0, u0)
+        f, u, sc = sim.get_fields(gpu_capi.CE_VEL_SYNC)
+        assert np.array_equal(f, f0.reshape(-1))
+        assert relmax(u, u0) <= 1e-12
+        assert sc.step == 0 and sc.t == 0.0 and sc.a == 1.0
+
+
+def test_checkpoint_roundtrip_is_bit_exact(gpu_capi):
+    for precision in ("f64", "f32"):
+        cfg = dict(dims=3, N=24, L=20.0, dt=0.05, nfields=2, q=(1.2,), expansion=True, precision=precision)
+        f0, u0 = lattice_ics(3, 24, 20.0, 2, q=(1.2,), seed=9)
+        with gpu_capi.Simulation(**cfg) as a, gpu_capi.Simulation(**cfg) as b:
+            a.set_fields(f0, u0)
+            a.step(37)
+            fs, vs, sc = a.get_fields(gpu_capi.CE_VEL_STAGGERED)
+            b.set_fields(fs, vs, gpu_capi.CE_VEL_STAGGERED, sc)
+            a.step(25)
+            b.step(25)
+            fa, va, sa = a.get_fields(gpu_capi.CE_VEL_STAGGERED)
+            fb, vb, sb = b.get_fields(gpu_capi.CE_VEL_STAGGERED)
+            assert np.array_equal(fa, fb) and np.array_equal(va, vb), precision
+            assert (sa.a, sa.ap_half, sa.app, sa.t, sa.step) == (sb.a, sb.ap_half, sb.app, sb.t, sb.step)
+
+
+def test_fp32_storage_error_against_fp64_oracle(gpu_capi, orc):
+    """FP32 fields/velocities with FP64 sums and a(t): statistics within 1e-3."""
+    dims, N, L, dt, nf, q = 3, 32, 20.0, 0.05, 2, (1.2,)
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, True, 100, precision="f32")
+    with sim:
+        ef = per_field_err(f, ref.f, nf)
+        ev = per_field_err(v, ref.v, nf)
+        assert ef < 1e-5 and ev < 1e-3, (ef, ev)
+        assert abs(sc.a - ref.scale.a) / ref.scale.a < 1e-6
+        en = sim.energy()
+        en_ref = orc.energy(ref)
+        assert en["E"] == pytest.approx(en_ref["E"], rel=1e-3)
+        mean, var = sim.means_variances()
+        mref, vref = orc.means_variances(ref.p, ref.f)
+        # a zero-mean field (chi) is judged against its spread, not its ~1e-11 mean
+        scale = np.maximum(np.abs(mref), np.sqrt(vref))
+        assert np.all(np.abs(mean - mref) <= 1e-3 * scale), (mean, mref, vref)
+        np.testing.assert_allclose(var, vref, rtol=1e-3)
+
+
+def test_nonfinite_state_is_reported_not_faulted(gpu_capi):
+    """A state whose potential overflows makes the global sums non-finite: the
+    device latches CE_ENONFINITE and the next synchronising call returns it."""
+    N = 8
+    f0 = np.zeros((2, N ** 3))
+    f0[0] = 1e200
+    u0 = np.zeros_like(f0)
+    with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=0.05, nfields=2, q=(1.2,), expansion=True) as sim:
+        with pytest.raises(gpu_capi.CeError) as ei:
+            sim.set_fields(f0, u0)
+        assert ei.value.code == gpu_capi.CE_ENONFINITE
+
+
+def test_step_before_set_fields_is_a_state_error(gpu_capi):
+    with gpu_capi.Simulation(dims=3, N=8, L=20.0, dt=0.05) as sim:
+        with pytest.raises(gpu_capi.CeError) as ei:
+            sim.step(1)
+        assert ei.value.code == gpu_capi.CE_ESTATE
+
+
+def test_zero_steps_and_torch_stream_and_allocator(gpu_capi, orc):
+    import torch
+    s = torch.cuda.Stream()
+    f0, u0 = lattice_ics(3, 16, 20.0, 2, q=(1.2,), seed=3)
+    with gpu_capi.Simulation(dims=3, N=16, L=20.0, dt=0.05, nfields=2, q=(1.2,), expansion=True,
+                             stream=s.cuda_stream, torch_allocator=True) as sim:
+        sim.set_fields(f0, u0)
+        sim.step(0)
+        sim.step(10)
+        f, v, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    p = orc.Params(dims=3, N=16, L=20.0, dt=0.05, nf=2, q=(1.2,), expansion=True)
+    ref = orc.step(orc.init(p, f0, u0), 10)
+    assert per_field_err(f, ref.f, 2) <= TOL64
