@@ -39,7 +39,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="3d_256cube_2field_expanding", dims=3, N=256, L=20.0, dt=0.02, nf=2,
                 q=(1.2,), expansion=True, phi0=1.0, seed=1)
 METRIC = "Gsite-updates/s"
-STEP_SOURCES = ("ce_sweep3d.cu", "ce_device.cuh", "ce_internal.h")
+STEP_SOURCES = {"k_step_sweep": ("ce_sweep3d.cu", "ce_device.cuh", "ce_internal.h"),
+                "k_step_generic": ("ce_generic.cu", "ce_device.cuh", "ce_internal.h")}
 
 
 def dist_env():
@@ -58,9 +59,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel_name: str) -> str:
     h = hashlib.sha1()
-    for name in STEP_SOURCES:
+    for name in STEP_SOURCES[kernel_name]:
         with open(os.path.join(ROOT, "paper_0712_0813_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -73,7 +74,7 @@ def ncu_traffic(kernel_name: str, precision: str):
     if not os.path.exists(path):
         return None
     pat = re.compile(rf"^traffic\s+{re.escape(kernel_name)}\s+{precision}\s+src=(\w+)\s+bytes_per_launch=(\d+)")
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel_name)
     with open(path) as fh:
         for line in fh:
             m = pat.match(line.strip())

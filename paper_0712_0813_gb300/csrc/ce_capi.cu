@@ -31,6 +31,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
+constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
 
 }  // namespace
 
@@ -56,6 +57,8 @@ struct ce_sim {
   int kernel = CE_KERNEL_GENERIC;
   int generic_blocks = 1;
   ce::SweepPlan plan{};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
+  bool graphs_ok = true;
   int64_t bytes = 0;
   struct Alloc {
     void* p;
@@ -147,6 +150,7 @@ ce::StepArgs<T> make_step_args(const ce_sim* s, int in, bool half_kick) {
   a.inv_S = 1.0 / (double)s->S;
   a.half_inv_dx2 = 0.5 / (s->dx * s->dx);
   a.update_scalars = (s->cfg.expansion && !half_kick) ? 1 : 0;
+  a.in_slot = in;
   a.sc_in = &s->aux->slot[in];
   a.sc_out = &s->aux->slot[in ^ 1];
   a.partials = s->partials;
@@ -165,6 +169,32 @@ cudaError_t launch_one_step(const ce_sim* s, int in, bool half_kick) {
 cudaError_t step_once(const ce_sim* s, int in, bool half_kick) {
   return s->prec == CE_F32 ? launch_one_step<float>(s, in, half_kick)
                            : launch_one_step<double>(s, in, half_kick);
+}
+
+// Capture kGraphSteps consecutive step launches starting from buffer set
+// `start` into a CUDA graph (built once per handle and parity, replayed by
+// ce_step).  Kernel arguments are fixed per handle, so the graph stays valid
+// for the handle's lifetime.
+cudaError_t ensure_graph(ce_sim* s, int start) {
+  if (s->graph[start]) return cudaSuccess;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  int in = start;
+  cudaError_t el = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && el == cudaSuccess; ++k) {
+    el = step_once(s, in, false);
+    in ^= 1;
+  }
+  e = cudaStreamEndCapture(s->stream, &g);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return el != cudaSuccess ? el : e;
+  }
+  e = cudaGraphInstantiate(&s->graph[start], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) s->graph[start] = nullptr;
+  return e;
 }
 
 template <typename T>
@@ -302,7 +332,6 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
   s->kernel = (cfg->kernel == CE_KERNEL_GENERIC || !sweep_ok) ? CE_KERNEL_GENERIC : CE_KERNEL_SWEEP;
   s->generic_blocks = ce::generic_blocks(S);
-  if (s->kernel == CE_KERNEL_SWEEP) s->plan = ce::sweep_plan(s->N, s->nf, s->prec);
   cudaGetDevice(&s->device);
   if (cfg->stream) {
     s->stream = static_cast<cudaStream_t>(cfg->stream);
@@ -323,6 +352,17 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
         return fail(CE_ENOMEM, "ce_create: device allocation of the lattice state failed");
       }
     }
+  if (s->kernel == CE_KERNEL_SWEEP) {
+    e = ce::sweep_prepare(s->plan, s->f, s->w, s->N, s->nf, s->prec, s->device);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (cfg->kernel == CE_KERNEL_SWEEP) {
+        ce_free(s);
+        return cuda_fail(e, "ce_create: z-sweep kernel set-up");
+      }
+      s->kernel = CE_KERNEL_GENERIC;   // e.g. a driver without tensor-map encoding
+    }
+  }
   int64_t sweep_blocks = s->kernel == CE_KERNEL_SWEEP ? (int64_t)s->plan.gx * s->plan.gy * s->plan.gz : 0;
   int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, sweep_blocks), 1);
   int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)ce::kDiagBlocksMax * 17);
@@ -348,6 +388,8 @@ void ce_free(ce_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& g : s->graph)
+    if (g) cudaGraphExecDestroy(g);
   release_all(s);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -413,6 +455,20 @@ int ce_step(ce_sim* s, int64_t n) {
   if (n < 0) return fail(CE_EINVAL, "ce_step: n must be >= 0");
   if (!s->have_state) return fail(CE_ESTATE, "ce_step: no fields set (call ce_set_fields first)");
   if ((rc = select_device(s))) return rc;
+  while (n >= kGraphSteps && s->graphs_ok) {
+    cudaError_t e = ensure_graph(s, s->cur);
+    if (e != cudaSuccess) {
+      // capture is unavailable on this stream (e.g. the legacy default stream): plain launches
+      cudaGetLastError();
+      s->graphs_ok = false;
+      break;
+    }
+    e = cudaGraphLaunch(s->graph[s->cur], s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ce_step: graph launch");
+    for (int k = 0; k < kGraphSteps; ++k) s->t = s->t + s->cfg.dt;
+    s->step += kGraphSteps;
+    n -= kGraphSteps;
+  }
   for (int64_t k = 0; k < n; ++k) {
     cudaError_t e = step_once(s, s->cur, false);
     if (e != cudaSuccess) return cuda_fail(e, "ce_step: launch");

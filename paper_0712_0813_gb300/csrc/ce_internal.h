@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "clusterlat.h"
@@ -75,6 +76,7 @@ struct StepArgs {
   double inv_S;
   double half_inv_dx2;
   int update_scalars;   // 1: reduce G, V and advance a, a', a'' in the last block
+  int in_slot;          // which ping-pong buffer set is the input (selects TMA maps)
   const DevScalars* sc_in;
   DevScalars* sc_out;
   double* partials;     // >= 2 * number of blocks
@@ -116,15 +118,27 @@ template <typename T> cudaError_t launch_to_f64(const T* src, double* dst, int64
 template <typename T> cudaError_t launch_vhalf_to_f64(const T* f, const T* w, const DevScalars* sc,
                                                       double* dst, int64_t n, cudaStream_t st);
 
-// 3D z-sweep kernel (sm_103a): availability check and launcher.
+// 3D z-sweep kernel (sm_103a).  TMA tensor maps of the input arrays, per
+// field and array (0 = f, 1 = w), for the three box heights the kernel loads:
+// TY+2 rows (interior tile), TY+1 rows (tile at the y edge), 1 row (the wrapped
+// halo row).  One set per ping-pong input buffer.
+struct SweepMaps {
+  CUtensorMap m[4][2][3];
+};
 struct SweepPlan {
-  int tx, ty, tz;         // tile extents (sites)
-  int gx, gy, gz;         // grid
+  int tx, ty;             // tile extents in x and y (sites)
+  int gx, gy, gz;         // grid: x tiles, y tiles, z chunks
   int threads;
+  int stages;
+  int blocks_per_sm;
   size_t smem;
+  SweepMaps maps[2];
 };
 bool sweep_supported(int dims, int64_t N, int nf, int prec);
-SweepPlan sweep_plan(int64_t N, int nf, int prec);
+// Encode the tensor maps for the state buffers and pick the grid.  Returns a
+// cudaError_t (cudaErrorNotSupported if the driver lacks tensor-map encoding).
+cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2][4], int64_t N, int nf,
+                          int prec, int device);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
 

@@ -173,3 +173,76 @@ def test_zero_steps_and_torch_stream_and_allocator(gpu_capi, orc):
     p = orc.Params(dims=3, N=16, L=20.0, dt=0.05, nf=2, q=(1.2,), expansion=True)
     ref = orc.step(orc.init(p, f0, u0), 10)
     assert per_field_err(f, ref.f, 2) <= TOL64
+
+
+# ---------------------------------------------------------------- z-sweep kernel
+
+@pytest.mark.parametrize("nf,q", [(1, ()), (2, (1.2,)), (3, (0.8, 5.0)), (4, (0.8, 5.0, 40.0))])
+def test_sweep_kernel_matches_generic_fp64(gpu_capi, nf, q):
+    """Decomposition invariance: the tiled z-sweep and the one-thread-per-site
+    kernel agree to rounding (their global sums are added in different orders)."""
+    N, dt = 64, 0.02
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=q, seed=4, amp=1e-2)
+    out = {}
+    for kernel in ("generic", "sweep"):
+        with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=dt, nfields=nf, q=q, expansion=True,
+                                 kernel=kernel) as sim:
+            assert sim.kernel == {"generic": 1, "sweep": 2}[kernel]
+            sim.set_fields(f0, u0)
+            sim.step(60)
+            out[kernel] = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    fg, vg, sg = out["generic"]
+    fs, vs, ss = out["sweep"]
+    assert per_field_err(fs, fg, nf) <= 1e-12
+    assert per_field_err(vs, vg, nf) <= 1e-12
+    assert abs(ss.a - sg.a) <= 1e-13 * sg.a
+
+
+def test_sweep_kernel_matches_generic_fp32(gpu_capi):
+    N, nf, q = 128, 2, (1.2,)
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=q, seed=6)
+    out = {}
+    for kernel in ("generic", "sweep"):
+        with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=0.02, nfields=nf, q=q, expansion=True,
+                                 precision="f32", kernel=kernel) as sim:
+            sim.set_fields(f0, u0)
+            sim.step(40)
+            out[kernel] = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    assert per_field_err(out["sweep"][0], out["generic"][0], nf) <= 1e-6
+    assert per_field_err(out["sweep"][1], out["generic"][1], nf) <= 1e-4
+
+
+@pytest.mark.parametrize("N,steps,nf,q", [(64, 100, 2, (1.2,)), (128, 10, 4, (0.8, 5.0, 40.0))])
+def test_sweep_kernel_fp64_vs_oracle(gpu_capi, orc, N, steps, nf, q):
+    dt = 0.02 if nf == 2 else 0.01
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, 3, N, 20.0, dt, nf, q, True, steps, kernel="sweep")
+    with sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
+        assert per_field_err(f, ref.f, nf) <= TOL64
+        assert per_field_err(v, ref.v, nf) <= TOL64
+        assert abs(sc.a - ref.scale.a) / ref.scale.a <= TOL64
+
+
+@pytest.mark.parametrize("precision,tol_f,tol_v", [("f32", 2e-6, 2e-5), ("f64", 1e-13, 1e-12)])
+def test_full_size_256cube_one_step_against_oracle(gpu_capi, orc, precision, tol_f, tol_v):
+    """The bench workload (3D 256^3, 2 fields, expansion, dt = 0.02) in the
+    launch configuration the bench times: after 20 GPU steps the exported
+    state is stepped once by the oracle (FP64) and once by the GPU, and every
+    site is compared."""
+    N, nf, q, dt, L = 256, 2, (1.2,), 0.02, 20.0
+    f0, u0 = lattice_ics(3, N, L, nf, q=q, seed=1)
+    with gpu_capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True,
+                             precision=precision) as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
+        sim.set_fields(f0, u0)
+        sim.step(20)
+        fs, vs, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+        sim.step(1)
+        f1, v1, sc1 = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    p = orc.Params(dims=3, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
+    st = orc.State(p, fs.copy(), vs.copy(), orc.Scale(sc.a, sc.ap_half, sc.app, sc.t, sc.step))
+    orc.step(st, 1)
+    assert per_field_err(f1, st.f, nf) <= tol_f
+    assert per_field_err(v1, st.v, nf) <= tol_v
+    assert abs(sc1.a - st.scale.a) <= 1e-12 * st.scale.a
+    assert abs(sc1.ap_half - st.scale.ap) <= 1e-9 * abs(st.scale.ap)
