@@ -183,6 +183,31 @@ int ce_kernel_in_use(const ce_sim* sim);
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int ce_version(void);
 
+/* Allocation-free per-field mean and population variance of field arrays the
+ * caller already holds in device memory.  The paper has no counterpart: this
+ * call exists for callers that cannot let a library allocate device memory --
+ * code whose HBM is owned by another allocator (a framework's caching
+ * allocator, or a fixed arena reserved at start-up, where an extra cudaMalloc
+ * fails or fragments the pool) and latency-critical loops that cannot afford
+ * the implicit device synchronisation of cudaMalloc/cudaFree.
+ *   f:         DEVICE pointer to nfields * n values, float32 (precision CE_F32)
+ *              or float64 (CE_F64); field i starts at element i * n.
+ *   mean, var: DEVICE pointers to nfields doubles each, written by the call.
+ *   stream:    cudaStream_t to run on (NULL: the legacy default stream).  The
+ *              call is asynchronous; read the outputs after that stream is done.
+ * Limits: 1 <= nfields <= 4 and 1 <= n <= 2^34; anything else is CE_EINVAL.
+ * Scratch: one static 64 KiB device array inside the library, held by every
+ * GPU that loads it until the process exits; the call makes no cudaMalloc,
+ * cudaFree or other allocating call.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  All calls share the array, so calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by the
+ * caller; each call overwrites every scratch value it reads, so nothing needs
+ * clearing between calls.
+ * Errors: CE_EINVAL (NULL pointer, limits), CE_ECUDA (set-up or launch). */
+int ce_moments_noalloc(const void* f, int precision, int64_t n, int nfields, void* stream,
+                       double* mean, double* var);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,7 +58,7 @@ _keepalive: dict = {}   # handle -> (config, ctypes callbacks, allocation table)
 # Every symbol the public header declares (checked by the test-suite).
 EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_variances",
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
-           "ce_kernel_in_use", "ce_version")
+           "ce_kernel_in_use", "ce_version", "ce_moments_noalloc")
 
 
 def lib_path() -> str:
@@ -91,6 +91,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_device_bytes": (ctypes.c_int64, [vp]),
         "ce_kernel_in_use": (ctypes.c_int, [vp]),
         "ce_version": (ctypes.c_int, []),
+        "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -221,6 +222,17 @@ def ce_kernel_in_use(sim) -> int:
 
 def ce_version() -> int:
     return load().ce_version()
+
+
+def ce_moments_noalloc(f_ptr: int, precision: int, n: int, nfields: int, stream: int | None,
+                       mean_ptr: int, var_ptr: int):
+    """Allocation-free moments of caller-owned device arrays (see clusterlat.h).
+
+    All pointers are device addresses (e.g. ``tensor.data_ptr()``); the call is
+    asynchronous on ``stream`` and allocates nothing on the device."""
+    _check(load().ce_moments_noalloc(ctypes.c_void_p(int(f_ptr)), int(precision), int(n), int(nfields),
+                                     ctypes.c_void_p(int(stream) if stream else 0),
+                                     ctypes.c_void_p(int(mean_ptr)), ctypes.c_void_p(int(var_ptr))))
 
 
 class Simulation:

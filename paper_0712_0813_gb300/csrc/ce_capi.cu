@@ -35,6 +35,8 @@ constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps 
 
 }  // namespace
 
+void ce::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct ce_sim {
   ce_config cfg;
   int dims = 0, nf = 0, prec = CE_F64;

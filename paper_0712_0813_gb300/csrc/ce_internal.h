@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -141,6 +142,9 @@ cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2]
                           int prec, int device);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
+
+// Set the thread-local message returned by ce_last_error().
+void set_last_error(const std::string& msg);
 
 constexpr int kGenericThreads = 256;
 int generic_blocks(int64_t S);
