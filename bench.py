@@ -141,16 +141,18 @@ def make_inputs(rank: int):
     return lattice_ics(w["dims"], w["N"], w["L"], w["nf"], phi0=w["phi0"], q=w["q"], seed=w["seed"] + rank)
 
 
-def sim_config(precision: str, stream):
+def sim_config(precision: str, stream, hints=None):
     w = WORKLOAD
-    return dict(dims=w["dims"], N=w["N"], L=w["L"], dt=w["dt"], nfields=w["nf"], q=w["q"],
-                expansion=w["expansion"], phi0=w["phi0"], precision=precision, stream=stream)
+    cfg = dict(dims=w["dims"], N=w["N"], L=w["L"], dt=w["dt"], nfields=w["nf"], q=w["q"],
+               expansion=w["expansion"], phi0=w["phi0"], precision=precision, stream=stream)
+    cfg.update(hints or {})
+    return cfg
 
 
-def time_device_steps(capi, torch, f0, u0, precision, steps, warmup, barrier, sampler_gpu=None):
+def time_device_steps(capi, torch, f0, u0, precision, steps, warmup, barrier, sampler_gpu=None, hints=None):
     """Device-resident timing: CUDA events on the library's stream around `steps` launches."""
     stream = torch.cuda.Stream()
-    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream))
+    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream, hints))
     sim.set_fields(f0, u0)
     sim.step(warmup)
     sim.synchronize()
@@ -174,11 +176,12 @@ def time_device_steps(capi, torch, f0, u0, precision, steps, warmup, barrier, sa
     sim.synchronize()  # surfaces any latched device error
     ms = e0.elapsed_time(e1)
     kernel = {1: "generic", 2: "sweep"}[sim.kernel]
+    plan = sim.sweep_plan
     sim.close()
-    return ms, kernel, clocks
+    return ms, kernel, clocks, plan
 
 
-def time_e2e(capi, torch, f0, u0, precision, steps):
+def time_e2e(capi, torch, f0, u0, precision, steps, hints=None):
     """End to end through the public API with pinned host buffers: upload of the
     initial state, start-up, `steps` steps, download of the final state."""
     nf, S = f0.shape
@@ -189,7 +192,7 @@ def time_e2e(capi, torch, f0, u0, precision, steps):
     pin_f[:] = f0.reshape(-1)
     pin_u[:] = u0.reshape(-1)
     stream = torch.cuda.Stream()
-    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream))
+    sim = capi.Simulation(**sim_config(precision, stream.cuda_stream, hints))
     sim.set_fields(pin_f, pin_u)  # warm (first-touch, module load)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -275,6 +278,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's default launch plan instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -313,20 +318,36 @@ def main():
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
 
-    ms, kernel, clocks = time_device_steps(capi, torch, f0, u0, args.precision, args.steps, args.warmup,
-                                           barrier, sampler_gpu=gpu_index if rank == 0 else None)
+    # launch-plan autotuning (outside the timed region)
+    hints, hints64, tune_info = None, None, None
+    if not args.no_autotune and w["dims"] == 3:
+        from paper_0712_0813_gb300 import autotune
+        common = dict(N=w["N"], L=w["L"], dt=w["dt"], nfields=w["nf"], q=w["q"], expansion=w["expansion"],
+                      phi0=w["phi0"])
+        t0 = time.perf_counter()
+        res = autotune.autotune_sweep(f0, u0, precision=args.precision, **common)
+        res64 = autotune.autotune_sweep(f0, u0, precision="f64", steps=10, warmup=3,
+                                        zchunks=[0, 8, 16], **common)
+        hints, hints64 = res.hints(), res64.hints()
+        tune_info = {"candidates": len(res.table) + len(res64.table), "seconds": time.perf_counter() - t0,
+                     "best": hints, "best_ms_per_step": res.ms_per_step,
+                     "table": [list(t) for t in res.table]}
+    ms, kernel, clocks, plan = time_device_steps(capi, torch, f0, u0, args.precision, args.steps, args.warmup,
+                                                 barrier, sampler_gpu=gpu_index if rank == 0 else None,
+                                                 hints=hints)
     ms = max_over_ranks(ms)
     secs = ms / 1e3
     value = ws * S * args.steps / secs / 1e9
 
     # plain FP64 path on the same lattice (context for the FP32/FP64 ratio)
-    ms64, kernel64, _ = time_device_steps(capi, torch, f0, u0, "f64", args.fp64_steps, args.warmup, barrier)
+    ms64, kernel64, _, plan64 = time_device_steps(capi, torch, f0, u0, "f64", args.fp64_steps, args.warmup,
+                                                  barrier, hints=hints64)
     ms64 = max_over_ranks(ms64)
     value64 = ws * S * args.fp64_steps / (ms64 / 1e3) / 1e9
 
     e2e = None
     if not args.no_e2e:
-        t_e2e, nbytes = time_e2e(capi, torch, f0, u0, args.precision, args.steps)
+        t_e2e, nbytes = time_e2e(capi, torch, f0, u0, args.precision, args.steps, hints=hints)
         t_e2e = max_over_ranks(t_e2e)
         e2e = {"value": ws * S * args.steps / t_e2e / 1e9, "unit": METRIC,
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
@@ -358,10 +379,13 @@ def main():
             "config": {"workload": w["name"], "N": w["N"], "fields": w["nf"], "expansion": w["expansion"],
                        "dt": w["dt"], "L": w["L"], "precision": args.precision,
                        "storage": "fields+velocities " + args.precision + ", global sums and a(t) f64",
-                       "kernel": kernel, "parallelism": "replicas" if ws > 1 else "single",
+                       "kernel": kernel, "sweep_plan": {"tile_rows": plan[0], "stages": plan[1],
+                                                         "zchunks": plan[2]},
+                       "autotune": tune_info,
+                       "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "state 4x larger than L2; no flush needed"},
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
-                           "kernel": kernel64, "f32_over_f64": value / value64},
+                           "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -97,6 +97,9 @@ typedef struct {
   int precision;         /* CE_F64 or CE_F32                                  */
   int kernel;            /* CE_KERNEL_*                                       */
   int flags;             /* CE_FLAG_*                                         */
+  int tile_rows;         /* z-sweep tile rows (8 or 16); 0 = automatic        */
+  int stages;            /* z-sweep TMA pipeline stages (3..5); 0 = automatic */
+  int zchunks;           /* z-sweep chunks per tile column; 0 = automatic     */
   void* stream;          /* cudaStream_t to issue work on; NULL = own stream  */
   ce_alloc_fn alloc;     /* optional device allocator                         */
   ce_release_fn release;
@@ -179,6 +182,10 @@ int64_t ce_device_bytes(const ce_sim* sim);
 
 /* Which kernel ce_step launches: CE_KERNEL_GENERIC or CE_KERNEL_SWEEP. */
 int ce_kernel_in_use(const ce_sim* sim);
+
+/* The z-sweep launch plan in use: tile rows, pipeline stages and z-chunks
+ * (all 0 when the generic kernel runs).  Errors: CE_EINVAL (NULL argument). */
+int ce_sweep_plan(const ce_sim* sim, int* rows, int* stages, int* zchunks);
 
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int ce_version(void);

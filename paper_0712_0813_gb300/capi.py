@@ -31,7 +31,8 @@ class ce_config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("nfields", ctypes.c_int), ("q", ctypes.c_double * 3),
                 ("expansion", ctypes.c_int), ("phi0_over_mpl", ctypes.c_double),
                 ("phi0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("flags", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("flags", ctypes.c_int), ("tile_rows", ctypes.c_int), ("stages", ctypes.c_int),
+                ("zchunks", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("release", RELEASE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -58,7 +59,7 @@ _keepalive: dict = {}   # handle -> (config, ctypes callbacks, allocation table)
 # Every symbol the public header declares (checked by the test-suite).
 EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_variances",
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
-           "ce_kernel_in_use", "ce_version", "ce_moments_noalloc")
+           "ce_kernel_in_use", "ce_sweep_plan", "ce_version", "ce_moments_noalloc")
 
 
 def lib_path() -> str:
@@ -90,6 +91,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_last_error": (ctypes.c_char_p, []),
         "ce_device_bytes": (ctypes.c_int64, [vp]),
         "ce_kernel_in_use": (ctypes.c_int, [vp]),
+        "ce_sweep_plan": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "ce_version": (ctypes.c_int, []),
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
     }
@@ -136,7 +138,8 @@ def _torch_hooks(table: dict):
 def ce_create(dims: int, N: int, L: float, dt: float, nfields: int = 2, q=(1.2,),
               expansion: bool = False, phi0_over_mpl: float = 0.342, phi0: float = 1.0,
               precision: str | int = "f64", kernel: str | int = "auto",
-              allow_unstable_dt: bool = False, stream=None, torch_allocator: bool = False):
+              allow_unstable_dt: bool = False, stream=None, torch_allocator: bool = False,
+              tile_rows: int = 0, stages: int = 0, zchunks: int = 0):
     """Create a simulation handle (see ce_create in clusterlat.h)."""
     lib = load()
     cfg = ce_config()
@@ -149,6 +152,7 @@ def ce_create(dims: int, N: int, L: float, dt: float, nfields: int = 2, q=(1.2,)
     cfg.precision = {"f64": CE_F64, "f32": CE_F32}.get(precision, precision)
     cfg.kernel = {"auto": CE_KERNEL_AUTO, "generic": CE_KERNEL_GENERIC, "sweep": CE_KERNEL_SWEEP}.get(kernel, kernel)
     cfg.flags = CE_FLAG_ALLOW_UNSTABLE_DT if allow_unstable_dt else 0
+    cfg.tile_rows, cfg.stages, cfg.zchunks = int(tile_rows), int(stages), int(zchunks)
     if stream is not None:
         cfg.stream = ctypes.c_void_p(int(stream))
     keep = [cfg]
@@ -220,6 +224,13 @@ def ce_kernel_in_use(sim) -> int:
     return load().ce_kernel_in_use(sim)
 
 
+def ce_sweep_plan(sim):
+    """(rows, stages, zchunks) of the z-sweep plan; zeros when the generic kernel runs."""
+    r, st, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().ce_sweep_plan(sim, ctypes.byref(r), ctypes.byref(st), ctypes.byref(z)))
+    return r.value, st.value, z.value
+
+
 def ce_version() -> int:
     return load().ce_version()
 
@@ -267,6 +278,10 @@ class Simulation:
     @property
     def kernel(self):
         return ce_kernel_in_use(self.handle)
+
+    @property
+    def sweep_plan(self):
+        return ce_sweep_plan(self.handle)
 
     def close(self):
         if self.handle is not None:

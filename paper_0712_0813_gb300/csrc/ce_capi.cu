@@ -114,6 +114,11 @@ int validate(const ce_config* c, int64_t* S_out) {
   if (c->expansion != 0 && c->expansion != 1) return fail(CE_EINVAL, "ce_create: expansion must be 0 or 1");
   if (!!c->alloc != !!c->release) return fail(CE_EINVAL, "ce_create: alloc and release hooks go together");
   if (!std::isfinite(c->phi0_over_mpl) || !std::isfinite(c->phi0)) return fail(CE_EINVAL, "ce_create: non-finite phi0");
+  if (c->tile_rows != 0 && c->tile_rows != 8 && c->tile_rows != 16)
+    return fail(CE_EINVAL, "ce_create: tile_rows must be 0, 8 or 16");
+  if (c->stages != 0 && (c->stages < 3 || c->stages > 5)) return fail(CE_EINVAL, "ce_create: stages must be 0 or 3..5");
+  if (c->zchunks < 0 || (c->zchunks > 0 && c->zchunks > c->N / 2))
+    return fail(CE_EINVAL, "ce_create: zchunks must be 0 or 1..N/2");
   // Leapfrog stability: dt < 2 / omega_max, omega_max^2 = 4 d / dx^2 + largest mass^2
   // (masses 3 phi0^2 and q_i phi0^2 around the homogeneous phi0).
   if (!(c->flags & CE_FLAG_ALLOW_UNSTABLE_DT)) {
@@ -311,7 +316,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   int64_t S = 0;
   int rc = validate(cfg, &S);
   if (rc != CE_OK) return rc;
-  const bool sweep_ok = ce::sweep_supported(cfg->dims, cfg->N, cfg->nfields, cfg->precision);
+  const bool sweep_ok = ce::sweep_supported(cfg->dims, cfg->N, cfg->nfields, cfg->precision) &&
+                        ce::sweep_hint_valid(cfg->N, cfg->nfields, cfg->precision, cfg->tile_rows, cfg->stages);
   if (cfg->kernel == CE_KERNEL_SWEEP && !sweep_ok)
     return fail(CE_EINVAL, "ce_create: the z-sweep kernel needs dims == 3 and N a multiple of its tile");
   int ndev = 0;
@@ -355,7 +361,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
       }
     }
   if (s->kernel == CE_KERNEL_SWEEP) {
-    e = ce::sweep_prepare(s->plan, s->f, s->w, s->N, s->nf, s->prec, s->device);
+    e = ce::sweep_prepare(s->plan, s->f, s->w, s->N, s->nf, s->prec, s->device, cfg->tile_rows, cfg->stages,
+                          cfg->zchunks);
     if (e != cudaSuccess) {
       cudaGetLastError();
       if (cfg->kernel == CE_KERNEL_SWEEP) {
@@ -584,5 +591,17 @@ int ce_get_fields(ce_sim* s, double* f, double* v, int mode, ce_scalars_t* sc) {
 int64_t ce_device_bytes(const ce_sim* s) { return s ? s->bytes : 0; }
 
 int ce_kernel_in_use(const ce_sim* s) { return s ? s->kernel : CE_KERNEL_GENERIC; }
+
+int ce_sweep_plan(const ce_sim* s, int* rows, int* stages, int* zchunks) {
+  if (!s || !rows || !stages || !zchunks) return fail(CE_EINVAL, "ce_sweep_plan: NULL argument");
+  if (s->kernel != CE_KERNEL_SWEEP) {
+    *rows = *stages = *zchunks = 0;
+    return CE_OK;
+  }
+  *rows = s->plan.ty;
+  *stages = s->plan.stages;
+  *zchunks = s->plan.gz;
+  return CE_OK;
+}
 
 }  // extern "C"

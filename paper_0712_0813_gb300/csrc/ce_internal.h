@@ -120,13 +120,15 @@ template <typename T> cudaError_t launch_vhalf_to_f64(const T* f, const T* w, co
                                                       double* dst, int64_t n, cudaStream_t st);
 
 // 3D z-sweep kernel (sm_103a).  TMA tensor maps of the input arrays, per
-// field and array (0 = f, 1 = w), for the three box heights the kernel loads:
-// TY+2 rows (interior tile), TY+1 rows (tile at the y edge), 1 row (the wrapped
-// halo row).  One set per ping-pong input buffer.
+// field and array (0 = f, 1 = w), for the four boxes the kernel loads:
+// TX x (TY+2) rows (interior tile), TX x (TY+1) (tile at the y edge), TX x 1
+// (the wrapped halo row), 16 bytes x TY (an x-halo column).  One set per
+// ping-pong input buffer.
 struct SweepMaps {
-  CUtensorMap m[4][2][3];
+  CUtensorMap m[4][2][4];
 };
 struct SweepPlan {
+  int variant;            // index into the compiled (rows, stages) variants
   int tx, ty;             // tile extents in x and y (sites)
   int gx, gy, gz;         // grid: x tiles, y tiles, z chunks
   int threads;
@@ -136,12 +138,23 @@ struct SweepPlan {
   SweepMaps maps[2];
 };
 bool sweep_supported(int dims, int64_t N, int nf, int prec);
-// Encode the tensor maps for the state buffers and pick the grid.  Returns a
-// cudaError_t (cudaErrorNotSupported if the driver lacks tensor-map encoding).
+// Whether some compiled variant matches the hints (0 = any).
+bool sweep_hint_valid(int64_t N, int nf, int prec, int rows, int stages);
+// Pick the variant (hints 0 = automatic), the grid and the z-chunks, and
+// encode the tensor maps of the state buffers.  Returns a cudaError_t
+// (cudaErrorNotSupported if the driver lacks tensor-map encoding).
 cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2][4], int64_t N, int nf,
-                          int prec, int device);
+                          int prec, int device, int rows_hint, int stages_hint, int zchunks_hint);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
+namespace sweep {
+cudaError_t launch_f32(int variant, const StepArgs<float>& a, const SweepMaps& m, dim3 grid, size_t smem,
+                       cudaStream_t st);
+cudaError_t launch_f64(int variant, const StepArgs<double>& a, const SweepMaps& m, dim3 grid, size_t smem,
+                       cudaStream_t st);
+const void* kernel_f32(int variant, int nf);
+const void* kernel_f64(int variant, int nf);
+}  // namespace sweep
 
 // Set the thread-local message returned by ce_last_error().
 void set_last_error(const std::string& msg);

@@ -1,0 +1,65 @@
+// ce_sweep3d_f64.cu -- instantiations of the 3D z-sweep step kernel for double
+// storage (every compiled (rows, stages) variant and field count); kept apart
+// from the float instantiations so the two compile in parallel.
+#include "ce_sweep3d.cuh"
+
+namespace ce {
+namespace sweep {
+namespace {
+
+template <int NF, int V>
+cudaError_t launch_v(const StepArgs<double>& a, const SweepMaps& m, dim3 grid, size_t smem, cudaStream_t st) {
+  constexpr int TY = kVariants[V].ty, NST = kVariants[V].stages;
+  k_step_sweep<double, NF, TY, NST><<<grid, 32 * (TY + 1), smem, st>>>(a, m);
+  return cudaGetLastError();
+}
+
+template <int NF, int V>
+const void* kptr_v() {
+  constexpr int TY = kVariants[V].ty, NST = kVariants[V].stages;
+  return reinterpret_cast<const void*>(&k_step_sweep<double, NF, TY, NST>);
+}
+
+template <int NF>
+cudaError_t launch_nf(int v, const StepArgs<double>& a, const SweepMaps& m, dim3 g, size_t smem, cudaStream_t st) {
+  switch (v) {
+    case 0: return launch_v<NF, 0>(a, m, g, smem, st);
+    case 1: return launch_v<NF, 1>(a, m, g, smem, st);
+    case 2: return launch_v<NF, 2>(a, m, g, smem, st);
+    default: return launch_v<NF, 3>(a, m, g, smem, st);
+  }
+}
+
+template <int NF>
+const void* kptr_nf(int v) {
+  switch (v) {
+    case 0: return kptr_v<NF, 0>();
+    case 1: return kptr_v<NF, 1>();
+    case 2: return kptr_v<NF, 2>();
+    default: return kptr_v<NF, 3>();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_f64(int variant, const StepArgs<double>& a, const SweepMaps& m, dim3 grid, size_t smem,
+                       cudaStream_t st) {
+  switch (a.nf) {
+    case 1: return launch_nf<1>(variant, a, m, grid, smem, st);
+    case 2: return launch_nf<2>(variant, a, m, grid, smem, st);
+    case 3: return launch_nf<3>(variant, a, m, grid, smem, st);
+    default: return launch_nf<4>(variant, a, m, grid, smem, st);
+  }
+}
+
+const void* kernel_f64(int variant, int nf) {
+  switch (nf) {
+    case 1: return kptr_nf<1>(variant);
+    case 2: return kptr_nf<2>(variant);
+    case 3: return kptr_nf<3>(variant);
+    default: return kptr_nf<4>(variant);
+  }
+}
+
+}  // namespace sweep
+}  // namespace ce

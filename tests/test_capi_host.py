@@ -61,6 +61,10 @@ BAD = [
     (dict(kernel=9), "kernel"),
     (dict(dims=3, N=1 << 12), "2^34"),
     (dict(dims=2, N=100, kernel="sweep"), "z-sweep"),
+    (dict(tile_rows=12), "tile_rows"),
+    (dict(stages=9), "stages"),
+    (dict(zchunks=-1), "zchunks"),
+    (dict(N=16, zchunks=9), "zchunks"),
 ]
 
 

@@ -246,3 +246,44 @@ def test_full_size_256cube_one_step_against_oracle(gpu_capi, orc, precision, tol
     assert per_field_err(v1, st.v, nf) <= tol_v
     assert abs(sc1.a - st.scale.a) <= 1e-12 * st.scale.a
     assert abs(sc1.ap_half - st.scale.ap) <= 1e-9 * abs(st.scale.ap)
+
+
+VARIANTS = [(8, 4), (8, 5), (16, 3), (16, 4)]
+
+
+@pytest.mark.parametrize("rows,stages", VARIANTS)
+@pytest.mark.parametrize("zchunks", [1, 3, 8])
+def test_sweep_variants_and_directions_match_generic_fp64(gpu_capi, rows, stages, zchunks):
+    """Every compiled (rows, stages) variant, with odd and even numbers of
+    z-chunks (neighbouring chunks sweep in opposite directions), agrees with
+    the one-thread-per-site kernel."""
+    N, nf, q = 64, 2, (1.2,)
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=q, seed=12, amp=1e-2)
+    out = {}
+    for kernel in ("generic", "sweep"):
+        kw = dict(tile_rows=rows, stages=stages, zchunks=zchunks) if kernel == "sweep" else {}
+        with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=0.02, nfields=nf, q=q, expansion=True,
+                                 kernel=kernel, **kw) as sim:
+            if kernel == "sweep":
+                assert sim.sweep_plan == (rows, stages, zchunks)
+            sim.set_fields(f0, u0)
+            sim.step(33)
+            out[kernel] = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    assert per_field_err(out["sweep"][0], out["generic"][0], nf) <= 1e-12
+    assert per_field_err(out["sweep"][1], out["generic"][1], nf) <= 1e-12
+    assert abs(out["sweep"][2].a - out["generic"][2].a) <= 1e-13 * out["generic"][2].a
+
+
+@pytest.mark.parametrize("rows,stages", VARIANTS)
+def test_sweep_variants_fp32_vs_oracle(gpu_capi, orc, rows, stages):
+    N, nf, q, dt = 128, 2, (1.2,), 0.02
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=q, seed=13)
+    p = orc.Params(dims=3, N=N, L=20.0, dt=dt, nf=nf, q=q, expansion=True)
+    ref = orc.step(orc.init(p, f0, u0), 5)
+    with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=dt, nfields=nf, q=q, expansion=True, precision="f32",
+                             kernel="sweep", tile_rows=rows, stages=stages, zchunks=5) as sim:
+        sim.set_fields(f0, u0)
+        sim.step(5)
+        f, v, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+    assert per_field_err(f, ref.f, nf) <= 2e-6
+    assert per_field_err(v, ref.v, nf) <= 2e-5
