@@ -205,6 +205,68 @@ def time_e2e(capi, torch, f0, u0, precision, steps, hints=None):
     return t1 - t0, nbytes
 
 
+def batched_leg(capi, torch, steps: int, warmup: int, seq_steps: int, hbm_peak: float):
+    """Mixed-size workload (96 lattices of 1D/2D/3D): the batched FP32 persistent
+    kernel against the same lattices stepped one by one with the plain FP64 path
+    and with the plain FP32 path (device-resident, CUDA events)."""
+    from paper_0712_0813_gb300 import workloads as W
+    specs = W.mixed_batch_specs()
+    ics = [W.make_ics(sp) for sp in specs]
+    total = sum(W.sites(sp) for sp in specs)
+    stream = torch.cuda.Stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sims = []
+    for sp, (f0, u0) in zip(specs, ics):
+        sim = capi.Simulation(**W.sim_kwargs(sp, "f32"), kernel="generic")
+        sim.set_fields(f0, u0)
+        sims.append(sim)
+    b = capi.Batch(sims, stream=stream.cuda_stream)
+    info = b.info
+    b.step(warmup)
+    b.synchronize()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.synchronize()
+    b.close()
+    for sim in sims:
+        sim.close()
+    batched = total * steps / (ms / 1e3) / 1e9
+
+    def sequential(precision: str, nsteps: int):
+        t_ms, site_steps = 0.0, 0
+        for sp, (f0, u0) in zip(specs, ics):
+            with capi.Simulation(**W.sim_kwargs(sp, precision), stream=stream.cuda_stream) as sim:
+                sim.set_fields(f0, u0)
+                sim.step(3)
+                sim.synchronize()
+                e0.record(stream)
+                sim.step(nsteps)
+                e1.record(stream)
+                e1.synchronize()
+                t_ms += e0.elapsed_time(e1)
+                site_steps += W.sites(sp) * nsteps
+        return site_steps / (t_ms / 1e3) / 1e9
+
+    fp64_seq = sequential("f64", seq_steps)
+    f32_seq = sequential("f32", seq_steps)
+    alg = 16 * 2 * total
+    achieved = alg / (ms / 1e3 / steps) / 1e9
+    return {"workload": "96 lattices: 32 x 1D 65536, 32 x 2D 1024^2, 32 x 3D side in {64..192}; 2 fields, "
+                        "per-lattice q, phi0, Courant dt, expansion on half",
+            "sites": total, "steps": steps, "ms_per_step": ms / steps, "items": info["items"],
+            "blocks": info["blocks"], "value_f32_batched": batched, "fp64_plain_sequential": fp64_seq,
+            "f32_plain_sequential": f32_seq, "batched_over_fp64_plain": batched / fp64_seq,
+            "sequential_steps": seq_steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "kernel": "k_step_batched",
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def cpu_oracle_rate(f0, u0, target_s: float, N_sample: int | None = None):
     """Sites/s of the CPU oracle (serial, 1 thread) on the bench model."""
     import oracle
@@ -278,6 +340,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batched leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default launch plan instead of the autotuned one")
     args = ap.parse_args()
@@ -363,6 +427,10 @@ def main():
                 "frac": achieved / hbm_peak, "traffic": ncu_traffic(kname, args.precision),
                 "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
 
+    batch = None
+    if not args.no_batch:
+        batch = batched_leg(capi, torch, args.batch_steps, max(args.warmup // 10, 3), 10, hbm_peak)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -387,6 +455,7 @@ def main():
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                            "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
             "roofline": roofline,
+            "batched_mix": batch,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

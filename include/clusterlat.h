@@ -187,6 +187,39 @@ int ce_kernel_in_use(const ce_sim* sim);
  * (all 0 when the generic kernel runs).  Errors: CE_EINVAL (NULL argument). */
 int ce_sweep_plan(const ce_sim* sim, int* rows, int* stages, int* zchunks);
 
+/* ---- batches: many lattices, one persistent launch per step ------------
+ * A batch groups existing handles (any mix of dimensions and sizes, same
+ * precision and number of fields, fields already set) and advances all of
+ * them together: each step is ONE launch of a persistent kernel whose CTAs
+ * pull work items (row segments of one lattice, swept along its slowest axis)
+ * from a queue; each lattice keeps its own scale factor, computed by the CTA
+ * that completes that lattice's last item.  Per site the arithmetic is the
+ * same fused staggered-leapfrog step as ce_step (Sec. III).  While a handle
+ * belongs to a batch, ce_step and ce_set_fields on it return CE_ESTATE; the
+ * read-out calls (ce_energy, ce_get_fields, ...) wait for the batch first.
+ * A lattice advanced alone in a batch and inside any mix gives bit-identical
+ * results (its items and their summation order do not depend on the mix). */
+typedef struct ce_batch ce_batch;
+
+/* sims: n handles; sweep_len: sites per item along the sweep axis (0 = 32);
+ * stream: cudaStream_t for the batch's work (NULL = its own stream).
+ * Errors: CE_EINVAL (mixed precision or field count, N not a multiple of 4
+ * (FP32) / 2 (FP64), duplicates), CE_ESTATE (a member without fields or
+ * already in a batch), CE_ECUDA. */
+int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, void* stream, ce_batch** out);
+
+/* Advance every member by n >= 0 steps (asynchronous, CUDA graphs of 32). */
+int ce_batch_step(ce_batch* b, int64_t n);
+
+/* Wait for the batch and report any member's latched device error. */
+int ce_batch_synchronize(ce_batch* b);
+
+/* Members, work items per step, persistent CTAs, total sites. */
+int ce_batch_info(const ce_batch* b, int* members, int* items, int* blocks, int64_t* sites);
+
+/* Release the batch (members stay valid with their current state).  NULL-safe. */
+void ce_batch_free(ce_batch* b);
+
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int ce_version(void);
 

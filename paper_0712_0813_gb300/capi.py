@@ -59,7 +59,8 @@ _keepalive: dict = {}   # handle -> (config, ctypes callbacks, allocation table)
 # Every symbol the public header declares (checked by the test-suite).
 EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_variances",
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
-           "ce_kernel_in_use", "ce_sweep_plan", "ce_version", "ce_moments_noalloc")
+           "ce_kernel_in_use", "ce_sweep_plan", "ce_version", "ce_moments_noalloc",
+           "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_info", "ce_batch_free")
 
 
 def lib_path() -> str:
@@ -94,6 +95,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_sweep_plan": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "ce_version": (ctypes.c_int, []),
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
+        "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, vp, P(vp)]),
+        "ce_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "ce_batch_synchronize": (ctypes.c_int, [vp]),
+        "ce_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                         P(ctypes.c_int64)]),
+        "ce_batch_free": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -244,6 +251,70 @@ def ce_moments_noalloc(f_ptr: int, precision: int, n: int, nfields: int, stream:
     _check(load().ce_moments_noalloc(ctypes.c_void_p(int(f_ptr)), int(precision), int(n), int(nfields),
                                      ctypes.c_void_p(int(stream) if stream else 0),
                                      ctypes.c_void_p(int(mean_ptr)), ctypes.c_void_p(int(var_ptr))))
+
+
+def ce_batch_create(sims, sweep_len: int = 0, stream=None):
+    """Group handles (ctypes handles or Simulation objects) into a batch."""
+    hs = [x.handle if isinstance(x, Simulation) else x for x in sims]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value for h in hs])
+    b = ctypes.c_void_p()
+    _check(load().ce_batch_create(arr, len(hs), int(sweep_len), ctypes.c_void_p(int(stream) if stream else 0),
+                                  ctypes.byref(b)))
+    return b
+
+
+def ce_batch_step(b, n: int):
+    _check(load().ce_batch_step(b, int(n)))
+
+
+def ce_batch_synchronize(b):
+    _check(load().ce_batch_synchronize(b))
+
+
+def ce_batch_info(b) -> dict:
+    m, it, bl, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(load().ce_batch_info(b, ctypes.byref(m), ctypes.byref(it), ctypes.byref(bl), ctypes.byref(st)))
+    return {"members": m.value, "items": it.value, "blocks": bl.value, "sites": st.value}
+
+
+def ce_batch_free(b):
+    if b is not None and getattr(b, "value", None):
+        load().ce_batch_free(b)
+
+
+class Batch:
+    """Owning wrapper around a batch: ``with Batch(sims) as b: b.step(n)``."""
+
+    def __init__(self, sims, sweep_len: int = 0, stream=None):
+        self.sims = list(sims)
+        self.handle = ce_batch_create(self.sims, sweep_len, stream)
+
+    def step(self, n):
+        ce_batch_step(self.handle, n)
+
+    def synchronize(self):
+        ce_batch_synchronize(self.handle)
+
+    @property
+    def info(self):
+        return ce_batch_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            ce_batch_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

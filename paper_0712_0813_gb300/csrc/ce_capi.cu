@@ -37,37 +37,6 @@ constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps 
 
 void ce::set_last_error(const std::string& msg) { g_err = msg; }
 
-struct ce_sim {
-  ce_config cfg;
-  int dims = 0, nf = 0, prec = CE_F64;
-  int64_t N = 0, S = 0;
-  size_t esize = 8;
-  double dx = 0.0, kappa2 = 0.0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  void* f[2][4] = {};
-  void* w[2][4] = {};
-  ce::DevAux* aux = nullptr;
-  double* partials = nullptr;
-  double* staging = nullptr;
-  int64_t chunk = 0;
-  int cur = 0;
-  bool have_state = false;
-  double t = 0.0;
-  int64_t step = 0;
-  int kernel = CE_KERNEL_GENERIC;
-  int generic_blocks = 1;
-  ce::SweepPlan plan{};
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
-  bool graphs_ok = true;
-  int64_t bytes = 0;
-  struct Alloc {
-    void* p;
-    size_t n;
-  };
-  std::vector<Alloc> allocs;
-};
 
 namespace {
 
@@ -296,8 +265,11 @@ int check_sim(const ce_sim* s, const char* fn) {
   return CE_OK;
 }
 
+// Make the handle's device current and, for a batch member, let the batch's
+// queued steps finish first (the member's own stream does not see them).
 int select_device(const ce_sim* s) {
   cudaError_t e = cudaSetDevice(s->device);
+  if (e == cudaSuccess && s->batch) e = ce::batch_wait(s->batch);
   return e == cudaSuccess ? CE_OK : cuda_fail(e, "cudaSetDevice");
 }
 
@@ -396,6 +368,7 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
 void ce_free(ce_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
+  if (s->batch) ce::batch_detach(s->batch, s);
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (auto& g : s->graph)
     if (g) cudaGraphExecDestroy(g);
@@ -409,6 +382,7 @@ int ce_set_fields(ce_sim* s, const double* f, const double* v, int mode, const c
   int rc = check_sim(s, "ce_set_fields");
   if (rc) return rc;
   if (!f || !v) return fail(CE_EINVAL, "ce_set_fields: f and v must be non-NULL");
+  if (s->batch) return fail(CE_ESTATE, "ce_set_fields: the handle is a member of a batch (free the batch first)");
   if (mode != CE_VEL_SYNC && mode != CE_VEL_STAGGERED) return fail(CE_EINVAL, "ce_set_fields: unknown mode");
   if (mode == CE_VEL_SYNC && sc) return fail(CE_EINVAL, "ce_set_fields: scalars are only taken with CE_VEL_STAGGERED");
   if (mode == CE_VEL_STAGGERED) {
@@ -463,6 +437,7 @@ int ce_step(ce_sim* s, int64_t n) {
   if (rc) return rc;
   if (n < 0) return fail(CE_EINVAL, "ce_step: n must be >= 0");
   if (!s->have_state) return fail(CE_ESTATE, "ce_step: no fields set (call ce_set_fields first)");
+  if (s->batch) return fail(CE_ESTATE, "ce_step: the handle is a member of a batch (use ce_batch_step)");
   if ((rc = select_device(s))) return rc;
   while (n >= kGraphSteps && s->graphs_ok) {
     cudaError_t e = ensure_graph(s, s->cur);

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -156,8 +157,53 @@ const void* kernel_f32(int variant, int nf);
 const void* kernel_f64(int variant, int nf);
 }  // namespace sweep
 
+}  // namespace ce
+
+struct ce_batch;
+
+// A simulation handle (opaque in the public header).
+struct ce_sim {
+  ce_config cfg;
+  int dims = 0, nf = 0, prec = CE_F64;
+  int64_t N = 0, S = 0;
+  size_t esize = 8;
+  double dx = 0.0, kappa2 = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  void* f[2][4] = {};
+  void* w[2][4] = {};
+  ce::DevAux* aux = nullptr;
+  double* partials = nullptr;
+  double* staging = nullptr;
+  int64_t chunk = 0;
+  int cur = 0;
+  bool have_state = false;
+  double t = 0.0;
+  int64_t step = 0;
+  int kernel = CE_KERNEL_GENERIC;
+  int generic_blocks = 1;
+  ce::SweepPlan plan{};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
+  bool graphs_ok = true;
+  int64_t bytes = 0;
+  ce_batch* batch = nullptr;   // set while the handle is a member of a batch
+  struct Alloc {
+    void* p;
+    size_t n;
+  };
+  std::vector<Alloc> allocs;
+};
+
+namespace ce {
+
 // Set the thread-local message returned by ce_last_error().
 void set_last_error(const std::string& msg);
+
+// Wait until the batch a handle belongs to has finished its queued steps.
+cudaError_t batch_wait(ce_batch* b);
+// A member is being freed: finish the batch's work and mark the batch unusable.
+void batch_detach(ce_batch* b, ce_sim* s);
 
 constexpr int kGenericThreads = 256;
 int generic_blocks(int64_t S);

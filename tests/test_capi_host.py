@@ -102,3 +102,12 @@ def test_struct_layouts_match_header(capi):
     assert ctypes.sizeof(capi.ce_scalars_t) == 40
     assert ctypes.sizeof(capi.ce_energy_t) == 8 * 15
     assert capi.ce_config.stream.offset % 8 == 0
+
+
+def test_batch_rejects_bad_arguments_without_device(capi):
+    lib = capi.load()
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.ce_batch_create(None, 0, 0, None, ctypes.byref(out)) == capi.CE_EINVAL
+    assert lib.ce_batch_step(None, 1) == capi.CE_EINVAL
+    lib.ce_batch_free(None)
