@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=300)
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batched leg")
     ap.add_argument("--no-autotune", action="store_true",
@@ -431,6 +432,12 @@ def main():
     if not args.no_batch:
         batch = batched_leg(capi, torch, args.batch_steps, max(args.warmup // 10, 3), 10, hbm_peak)
 
+    serving = None
+    if args.serve_jobs > 0 and rank == 0:
+        from paper_0712_0813_gb300 import serve
+        cap = batch["value_f32_batched"] * 1e9 if batch else None
+        serving = serve.run_serving_benchmark(n_jobs=args.serve_jobs, capacity=cap)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -456,6 +463,7 @@ def main():
                            "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
             "roofline": roofline,
             "batched_mix": batch,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

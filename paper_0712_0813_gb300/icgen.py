@@ -37,8 +37,14 @@ def mode_grid(dims: int, N: int) -> np.ndarray:
 
 def lattice_ics(dims: int, N: int, L: float, nf: int, phi0: float = 1.0,
                 q=(1.2,), amp: float = 1e-4, seed: int = 1,
-                kcut_frac: float = 0.25):
-    """Return (f, u) as float64 arrays of shape (nf, N**dims), layout [field][z][y][x]."""
+                kcut_frac: float = 0.25, backend: str = "numpy"):
+    """Return (f, u) as float64 arrays of shape (nf, N**dims), layout [field][z][y][x].
+
+    backend "numpy" transforms on the host; "torch" draws the same phases and
+    runs the inverse FFT with torch (on the GPU when one is present), which is
+    what large lattices (512^3 and up) need."""
+    if backend == "torch":
+        return _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac)
     shape = (N,) * dims
     S = N ** dims
     n2 = mode_grid(dims, N)
@@ -59,6 +65,34 @@ def lattice_ics(dims: int, N: int, L: float, nf: int, phi0: float = 1.0,
         du = np.fft.irfftn(omega * c, s=shape, axes=tuple(range(dims))) * scale
         f[i] = (phi0 if i == 0 else 0.0) + df.reshape(-1)
         u[i] = du.reshape(-1)
+    return f, u
+
+
+def _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac):
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    shape = (N,) * dims
+    S = N ** dims
+    n2 = torch.as_tensor(mode_grid(dims, N), device=dev)
+    k = 2.0 * math.pi * torch.sqrt(n2) / L
+    keep = (n2 > 0) & (torch.sqrt(n2) <= kcut_frac * N)
+    f = np.empty((nf, S))
+    u = np.empty((nf, S))
+    qs = list(q) + [0.0] * 4
+    scale = amp * math.sqrt(S)
+    for i in range(nf):
+        m2 = 3.0 * phi0 * phi0 if i == 0 else qs[i - 1] * phi0 * phi0
+        omega = torch.sqrt(k * k + m2)
+        rng = np.random.default_rng([seed, i])
+        theta = torch.as_tensor(rng.uniform(0.0, 2.0 * math.pi, size=tuple(n2.shape)), device=dev)
+        amp_k = torch.where(keep, torch.sqrt(1.0 / (2.0 * omega)), torch.zeros_like(omega))
+        c = torch.polar(amp_k, theta)
+        axes = tuple(range(dims))
+        df = torch.fft.irfftn(c, s=shape, dim=axes) * scale
+        du = torch.fft.irfftn(omega * c, s=shape, dim=axes) * scale
+        f[i] = (phi0 if i == 0 else 0.0) + df.reshape(-1).cpu().numpy()
+        u[i] = du.reshape(-1).cpu().numpy()
+        del c, df, du, theta, amp_k, omega
     return f, u
 
 

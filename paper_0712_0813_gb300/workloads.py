@@ -6,7 +6,8 @@ lattices of 1024^2 and 32 3D lattices with side drawn uniformly from
 phi0 uniform in [0.5, 2], takes dt from its own Courant limit
 (`icgen.courant_dt`), has expansion on for even indices, box L = 20, two fields.
 `serving_job_specs` draws jobs for the serving loop from the same mix plus 5%
-3D 512^3 lattices, with 2000-20000 steps each.
+3D 512^3 lattices (round(5% of the jobs), at least one from 10 jobs up, at
+seeded positions), with 2000-20000 steps each.
 """
 from __future__ import annotations
 
@@ -46,9 +47,13 @@ def serving_job_specs(n_jobs: int, seed: int = 4, big_fraction: float = 0.05,
                       steps_range=(2000, 20000), big_side: int = 512) -> list:
     rng = np.random.default_rng(seed)
     base = mixed_batch_specs(seed=seed)
+    n_big = int(round(big_fraction * n_jobs))
+    if n_jobs >= 10:
+        n_big = max(1, n_big)
+    big = set(rng.choice(n_jobs, size=n_big, replace=False).tolist()) if n_big else set()
     jobs = []
     for j in range(n_jobs):
-        if rng.uniform() < big_fraction:
+        if j in big:
             spec = _spec(rng, 3, big_side, j, seed + 100)
         else:
             spec = dict(base[int(rng.integers(len(base)))])
@@ -69,8 +74,9 @@ def state_bytes(spec: dict, precision: str = "f32") -> int:
 
 
 def make_ics(spec: dict):
+    big = sites(spec) >= 1 << 24
     return lattice_ics(spec["dims"], spec["N"], spec["L"], spec["nf"], phi0=spec["phi0"], q=spec["q"],
-                       seed=spec["seed"])
+                       seed=spec["seed"], backend="torch" if big else "numpy")
 
 
 def sim_kwargs(spec: dict, precision: str = "f32") -> dict:
