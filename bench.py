@@ -36,10 +36,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="3d_256cube_2field_expanding", dims=3, N=256, L=20.0, dt=0.02, nf=2,
-                q=(1.2,), expansion=True, phi0=1.0, seed=1)
+def _courant(N, q):
+    from paper_0712_0813_gb300.icgen import courant_dt
+    return courant_dt(3, N, 20.0, 1.0, q)
+
+
+# 256cube is the default (the bench line); the others are the large-lattice configurations.
+WORKLOADS = {
+    "256cube": dict(name="3d_256cube_2field_expanding", dims=3, N=256, L=20.0, dt=0.02, nf=2,
+                    q=(1.2,), expansion=True, phi0=1.0, seed=1, steps=5000),
+    "1024cube": dict(name="3d_1024cube_2field_expanding", dims=3, N=1024, L=20.0, dt=None, nf=2,
+                     q=(1.2,), expansion=True, phi0=1.0, seed=1, steps=2000),
+    "512cube_4field": dict(name="3d_512cube_4field_expanding", dims=3, N=512, L=20.0, dt=None, nf=4,
+                           q=(0.8, 5.0, 40.0), expansion=True, phi0=1.0, seed=1, steps=1000),
+}
+WORKLOAD = WORKLOADS["256cube"]
 METRIC = "Gsite-updates/s"
-STEP_SOURCES = {"k_step_sweep": ("ce_sweep3d.cu", "ce_device.cuh", "ce_internal.h"),
+STEP_SOURCES = {"k_step_sweep": ("ce_sweep3d.cuh", "ce_sweep3d_f32.cu", "ce_device.cuh", "ce_internal.h"),
                 "k_step_generic": ("ce_generic.cu", "ce_device.cuh", "ce_internal.h")}
 
 
@@ -138,7 +151,10 @@ class ClockSampler:
 def make_inputs(rank: int):
     from paper_0712_0813_gb300.icgen import lattice_ics
     w = WORKLOAD
-    return lattice_ics(w["dims"], w["N"], w["L"], w["nf"], phi0=w["phi0"], q=w["q"], seed=w["seed"] + rank)
+    big = w["N"] ** w["dims"] >= 1 << 24
+    from paper_0712_0813_gb300.replicas import replica_seed
+    return lattice_ics(w["dims"], w["N"], w["L"], w["nf"], phi0=w["phi0"], q=w["q"],
+                       seed=replica_seed(w["seed"], rank), backend="torch" if big else "numpy")
 
 
 def sim_config(precision: str, stream, hints=None):
@@ -187,14 +203,15 @@ def time_e2e(capi, torch, f0, u0, precision, steps, hints=None):
     nf, S = f0.shape
     pin_f = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
     pin_u = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
-    out_f = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
-    out_v = torch.empty(nf * S, dtype=torch.float64, pin_memory=True).numpy()
+    out_f, out_v = pin_f, pin_u          # the inputs are consumed by set_fields: reuse them for the outputs
     pin_f[:] = f0.reshape(-1)
     pin_u[:] = u0.reshape(-1)
     stream = torch.cuda.Stream()
     sim = capi.Simulation(**sim_config(precision, stream.cuda_stream, hints))
     sim.set_fields(pin_f, pin_u)  # warm (first-touch, module load)
     torch.cuda.synchronize()
+    pin_f[:] = f0.reshape(-1)
+    pin_u[:] = u0.reshape(-1)
     t0 = time.perf_counter()
     sim.set_fields(pin_f, pin_u)
     sim.step(steps)
@@ -332,7 +349,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--workload", default="256cube", choices=sorted(WORKLOADS))
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: the workload's)")
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
@@ -343,11 +361,23 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=300)
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batched leg")
+    ap.add_argument("--plan", default=None,
+                    help="force the z-sweep plan rows,stages,zchunks for the FP32 leg (skips autotuning)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default launch plan instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global WORKLOAD
+    WORKLOAD = dict(WORKLOADS[args.workload])
+    if WORKLOAD["dt"] is None:
+        WORKLOAD["dt"] = _courant(WORKLOAD["N"], WORKLOAD["q"])
+    if args.steps is None:
+        args.steps = WORKLOAD["steps"]
+    if args.workload != "256cube":
+        args.no_batch = True
+        args.serve_jobs = 0
+        args.fp64_steps = min(args.fp64_steps, 20)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -362,16 +392,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    from paper_0712_0813_gb300 import replicas
+
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        replicas.barrier(dist)
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dist, device="cuda")
 
     from paper_0712_0813_gb300 import build as pkg_build
     pkg_build.build()
@@ -385,14 +412,19 @@ def main():
 
     # launch-plan autotuning (outside the timed region)
     hints, hints64, tune_info = None, None, None
-    if not args.no_autotune and w["dims"] == 3:
+    if args.plan:
+        r_, s_, z_ = (int(x) for x in args.plan.split(","))
+        hints = {"tile_rows": r_, "stages": s_, "zchunks": z_}
+        tune_info = {"forced": hints}
+    elif not args.no_autotune and w["dims"] == 3:
         from paper_0712_0813_gb300 import autotune
         common = dict(N=w["N"], L=w["L"], dt=w["dt"], nfields=w["nf"], q=w["q"], expansion=w["expansion"],
                       phi0=w["phi0"])
         t0 = time.perf_counter()
         res = autotune.autotune_sweep(f0, u0, precision=args.precision, **common)
-        res64 = autotune.autotune_sweep(f0, u0, precision="f64", steps=10, warmup=3,
-                                        zchunks=[0, 8, 16], **common)
+        res64 = autotune.autotune_sweep(f0, u0, precision="f64", steps=4 if w["N"] > 256 else 10, warmup=2,
+                                        repeats=1, zchunks=[0, 8, 16] if w["N"] <= 256 else [0, 2],
+                                        **common)
         hints, hints64 = res.hints(), res64.hints()
         tune_info = {"candidates": len(res.table) + len(res64.table), "seconds": time.perf_counter() - t0,
                      "best": hints, "best_ms_per_step": res.ms_per_step,
@@ -402,7 +434,7 @@ def main():
                                                  hints=hints)
     ms = max_over_ranks(ms)
     secs = ms / 1e3
-    value = ws * S * args.steps / secs / 1e9
+    value = replicas.aggregate_throughput(ws, S * args.steps, secs) / 1e9
 
     # plain FP64 path on the same lattice (context for the FP32/FP64 ratio)
     ms64, kernel64, _, plan64 = time_device_steps(capi, torch, f0, u0, "f64", args.fp64_steps, args.warmup,
@@ -442,7 +474,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, k, Ns, el = cpu_oracle_rate(f0, u0, args.cpu_seconds)
+        Ns_sample = 256 if w["N"] > 256 else None    # a bounded sample of the large lattices
+        rate, k, Ns, el = cpu_oracle_rate(f0, u0, args.cpu_seconds, N_sample=Ns_sample)
         cpu = {"value": rate / 1e9, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"{k} oracle steps of the full {Ns}^3 lattice ({el:.1f} s, serial FP64 C)"}
 
@@ -458,7 +491,7 @@ def main():
                                                          "zchunks": plan[2]},
                        "autotune": tune_info,
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "state 4x larger than L2; no flush needed"},
+                       "l2": f"state {4 * esize * w['nf'] * S / 1e6:.0f} MB > L2 (129 MB); no flush needed"},
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                            "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
             "roofline": roofline,

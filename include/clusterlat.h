@@ -75,6 +75,11 @@ extern "C" {
 
 /* ---- config flags ---------------------------------------------------- */
 #define CE_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt < 2/omega_max check       */
+#define CE_FLAG_TEST_TMA_STALL    2  /* failure-detection tests only: every plane
+                                        the z-sweep kernel loads announces 16 bytes
+                                        that never arrive, so its bounded waits run
+                                        out (~0.5 ms) and each launch latches
+                                        CE_ETIMEOUT; no GPU fault is involved     */
 
 /* Device allocator hooks (optional).  alloc returns a device pointer of at
  * least `bytes` (256-byte aligned) usable on `stream`, or NULL; release
@@ -97,7 +102,7 @@ typedef struct {
   int precision;         /* CE_F64 or CE_F32                                  */
   int kernel;            /* CE_KERNEL_*                                       */
   int flags;             /* CE_FLAG_*                                         */
-  int tile_rows;         /* z-sweep tile rows (8 or 16); 0 = automatic        */
+  int tile_rows;         /* z-sweep tile rows (4, 8 or 16); 0 = automatic     */
   int stages;            /* z-sweep TMA pipeline stages (3..5); 0 = automatic */
   int zchunks;           /* z-sweep chunks per tile column; 0 = automatic     */
   void* stream;          /* cudaStream_t to issue work on; NULL = own stream  */
@@ -186,6 +191,11 @@ int ce_kernel_in_use(const ce_sim* sim);
 /* The z-sweep launch plan in use: tile rows, pipeline stages and z-chunks
  * (all 0 when the generic kernel runs).  Errors: CE_EINVAL (NULL argument). */
 int ce_sweep_plan(const ce_sim* sim, int* rows, int* stages, int* zchunks);
+
+/* Switch the z-sweep launch plan of an existing handle (0 = automatic); the
+ * state is kept.  Synchronises.  Errors: CE_EINVAL (no z-sweep kernel on this
+ * handle, or no compiled variant matches), CE_ESTATE (member of a batch). */
+int ce_replan(ce_sim* sim, int rows, int stages, int zchunks);
 
 /* ---- batches: many lattices, one persistent launch per step ------------
  * A batch groups existing handles (any mix of dimensions and sizes, same

@@ -4,8 +4,8 @@ The kernel is compiled in several variants (tile rows x TMA pipeline stages)
 and splits each tile column into z-chunks; which combination streams HBM best
 depends on the lattice size, the number of fields and the precision.  The
 autotuner times each candidate on the caller's own lattice through the public
-C ABI (ce_create with the tile_rows / stages / zchunks hints, ce_set_fields,
-ce_step) with CUDA events, and returns the fastest.  Results are cached per
+C ABI (one handle, ce_replan between candidates, ce_step timed with CUDA
+events) and returns the fastest.  Results are cached per
 (N, nfields, precision, expansion) for the process; `save`/`load` persist them.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 from . import capi
 
-VARIANTS = ((8, 4), (8, 5), (16, 3), (16, 4))
+VARIANTS = ((8, 4), (8, 5), (16, 3), (16, 4), (4, 4), (4, 5))
 _cache: dict = {}
 
 
@@ -37,33 +37,38 @@ def _key(N, nfields, precision, expansion):
 
 
 def zchunk_candidates(N: int) -> list:
-    base = [0, 4, 6, 8, 10, 12, 14, 16, 19, 24, 32, 38]
+    if N >= 512:       # the grid is already many waves deep; a few short columns suffice
+        base = [0, 1, 2, 4, 8]
+    else:
+        base = [0, 4, 6, 8, 10, 12, 14, 16, 19, 24, 32, 38]
     return [z for z in base if z == 0 or z <= N // 2]
 
 
 def autotune_sweep(f0, u0, *, N: int, L: float, dt: float, nfields: int, q, expansion: bool,
                    precision: str = "f32", phi0: float = 1.0, steps: int = 40, warmup: int = 8,
                    repeats: int = 2, zchunks=None, variants=VARIANTS, use_cache: bool = True) -> TuneResult:
-    """Time every applicable (tile_rows, stages, zchunks) on the given 3D state."""
+    """Time every applicable (tile_rows, stages, zchunks) on the given 3D state.
+
+    One handle holds the state; `ce_replan` switches its launch plan between
+    candidates, so large lattices are uploaded once."""
     import torch
     key = _key(N, nfields, precision, expansion)
     if use_cache and key in _cache:
         return _cache[key]
     stream = torch.cuda.Stream()
     table = []
-    for rows, stages in variants:
-        for zc in (zchunks if zchunks is not None else zchunk_candidates(N)):
-            try:
-                sim = capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nfields, q=q, expansion=expansion,
-                                      phi0=phi0, precision=precision, kernel="sweep", stream=stream.cuda_stream,
-                                      tile_rows=rows, stages=stages, zchunks=zc)
-            except capi.CeError as e:
-                if e.code == capi.CE_EINVAL:
-                    continue          # this variant does not apply to the lattice
-                raise
-            with sim:
+    with capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nfields, q=q, expansion=expansion, phi0=phi0,
+                         precision=precision, kernel="sweep", stream=stream.cuda_stream) as sim:
+        sim.set_fields(f0, u0)
+        for rows, stages in variants:
+            for zc in (zchunks if zchunks is not None else zchunk_candidates(N)):
+                try:
+                    sim.replan(rows, stages, zc)
+                except capi.CeError as e:
+                    if e.code == capi.CE_EINVAL:
+                        continue          # this variant does not apply to the lattice
+                    raise
                 plan = sim.sweep_plan
-                sim.set_fields(f0, u0)
                 sim.step(warmup)
                 best = float("inf")
                 for _ in range(repeats):
@@ -75,11 +80,11 @@ def autotune_sweep(f0, u0, *, N: int, L: float, dt: float, nfields: int, q, expa
                     e1.synchronize()
                     best = min(best, e0.elapsed_time(e1) / steps)
                 sim.synchronize()
-            table.append((plan[0], plan[1], plan[2], best))
+                table.append((plan[0], plan[1], plan[2], best))
     if not table:
         raise capi.CeError(capi.CE_EINVAL, "no z-sweep variant applies to this lattice")
-    r, s, z, ms = min(table, key=lambda t: t[3])
-    res = TuneResult(r, s, z, ms, table)
+    r, s_, z, ms = min(table, key=lambda t: t[3])
+    res = TuneResult(r, s_, z, ms, table)
     _cache[key] = res
     return res
 

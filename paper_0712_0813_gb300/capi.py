@@ -21,6 +21,7 @@ CE_F64, CE_F32 = 0, 1
 CE_VEL_SYNC, CE_VEL_STAGGERED = 0, 1
 CE_KERNEL_AUTO, CE_KERNEL_GENERIC, CE_KERNEL_SWEEP = 0, 1, 2
 CE_FLAG_ALLOW_UNSTABLE_DT = 1
+CE_FLAG_TEST_TMA_STALL = 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -59,7 +60,7 @@ _keepalive: dict = {}   # handle -> (config, ctypes callbacks, allocation table)
 # Every symbol the public header declares (checked by the test-suite).
 EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_variances",
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
-           "ce_kernel_in_use", "ce_sweep_plan", "ce_version", "ce_moments_noalloc",
+           "ce_kernel_in_use", "ce_sweep_plan", "ce_replan", "ce_version", "ce_moments_noalloc",
            "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_info", "ce_batch_free")
 
 
@@ -93,6 +94,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_device_bytes": (ctypes.c_int64, [vp]),
         "ce_kernel_in_use": (ctypes.c_int, [vp]),
         "ce_sweep_plan": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "ce_replan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ce_version": (ctypes.c_int, []),
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
         "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, vp, P(vp)]),
@@ -146,7 +148,7 @@ def ce_create(dims: int, N: int, L: float, dt: float, nfields: int = 2, q=(1.2,)
               expansion: bool = False, phi0_over_mpl: float = 0.342, phi0: float = 1.0,
               precision: str | int = "f64", kernel: str | int = "auto",
               allow_unstable_dt: bool = False, stream=None, torch_allocator: bool = False,
-              tile_rows: int = 0, stages: int = 0, zchunks: int = 0):
+              tile_rows: int = 0, stages: int = 0, zchunks: int = 0, flags: int = 0):
     """Create a simulation handle (see ce_create in clusterlat.h)."""
     lib = load()
     cfg = ce_config()
@@ -158,7 +160,7 @@ def ce_create(dims: int, N: int, L: float, dt: float, nfields: int = 2, q=(1.2,)
     cfg.phi0 = float(phi0)
     cfg.precision = {"f64": CE_F64, "f32": CE_F32}.get(precision, precision)
     cfg.kernel = {"auto": CE_KERNEL_AUTO, "generic": CE_KERNEL_GENERIC, "sweep": CE_KERNEL_SWEEP}.get(kernel, kernel)
-    cfg.flags = CE_FLAG_ALLOW_UNSTABLE_DT if allow_unstable_dt else 0
+    cfg.flags = (CE_FLAG_ALLOW_UNSTABLE_DT if allow_unstable_dt else 0) | int(flags)
     cfg.tile_rows, cfg.stages, cfg.zchunks = int(tile_rows), int(stages), int(zchunks)
     if stream is not None:
         cfg.stream = ctypes.c_void_p(int(stream))
@@ -236,6 +238,10 @@ def ce_sweep_plan(sim):
     r, st, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().ce_sweep_plan(sim, ctypes.byref(r), ctypes.byref(st), ctypes.byref(z)))
     return r.value, st.value, z.value
+
+
+def ce_replan(sim, rows: int = 0, stages: int = 0, zchunks: int = 0):
+    _check(load().ce_replan(sim, int(rows), int(stages), int(zchunks)))
 
 
 def ce_version() -> int:
@@ -353,6 +359,9 @@ class Simulation:
     @property
     def sweep_plan(self):
         return ce_sweep_plan(self.handle)
+
+    def replan(self, rows: int = 0, stages: int = 0, zchunks: int = 0):
+        ce_replan(self.handle, rows, stages, zchunks)
 
     def close(self):
         if self.handle is not None:

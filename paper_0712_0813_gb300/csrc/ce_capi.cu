@@ -32,6 +32,7 @@ constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
 constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device-side wait
 
 }  // namespace
 
@@ -83,8 +84,8 @@ int validate(const ce_config* c, int64_t* S_out) {
   if (c->expansion != 0 && c->expansion != 1) return fail(CE_EINVAL, "ce_create: expansion must be 0 or 1");
   if (!!c->alloc != !!c->release) return fail(CE_EINVAL, "ce_create: alloc and release hooks go together");
   if (!std::isfinite(c->phi0_over_mpl) || !std::isfinite(c->phi0)) return fail(CE_EINVAL, "ce_create: non-finite phi0");
-  if (c->tile_rows != 0 && c->tile_rows != 8 && c->tile_rows != 16)
-    return fail(CE_EINVAL, "ce_create: tile_rows must be 0, 8 or 16");
+  if (c->tile_rows != 0 && c->tile_rows != 4 && c->tile_rows != 8 && c->tile_rows != 16)
+    return fail(CE_EINVAL, "ce_create: tile_rows must be 0, 4, 8 or 16");
   if (c->stages != 0 && (c->stages < 3 || c->stages > 5)) return fail(CE_EINVAL, "ce_create: stages must be 0 or 3..5");
   if (c->zchunks < 0 || (c->zchunks > 0 && c->zchunks > c->N / 2))
     return fail(CE_EINVAL, "ce_create: zchunks must be 0 or 1..N/2");
@@ -127,6 +128,9 @@ ce::StepArgs<T> make_step_args(const ce_sim* s, int in, bool half_kick) {
   a.half_inv_dx2 = 0.5 / (s->dx * s->dx);
   a.update_scalars = (s->cfg.expansion && !half_kick) ? 1 : 0;
   a.in_slot = in;
+  const bool stall = (s->cfg.flags & CE_FLAG_TEST_TMA_STALL) != 0;
+  a.wait_cycles = stall ? (1LL << 20) : kWaitCycles;
+  a.missing_tx = stall ? 16u : 0u;
   a.sc_in = &s->aux->slot[in];
   a.sc_out = &s->aux->slot[in ^ 1];
   a.partials = s->partials;
@@ -344,7 +348,12 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
       s->kernel = CE_KERNEL_GENERIC;   // e.g. a driver without tensor-map encoding
     }
   }
-  int64_t sweep_blocks = s->kernel == CE_KERNEL_SWEEP ? (int64_t)s->plan.gx * s->plan.gy * s->plan.gz : 0;
+  // partial sums: room for the largest grid any z-sweep plan can use (8-row tiles, N/2 z-chunks)
+  int64_t sweep_blocks = 0;
+  if (s->kernel == CE_KERNEL_SWEEP) {
+    const int64_t tx = s->prec == CE_F32 ? 128 : 64;
+    sweep_blocks = std::max<int64_t>((int64_t)s->plan.gx * s->plan.gy * s->plan.gz, (s->N / tx) * (s->N / 4) * (s->N / 2));
+  }
   int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, sweep_blocks), 1);
   int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)ce::kDiagBlocksMax * 17);
   s->partials = static_cast<double*>(dalloc(s, (size_t)plen * 8));
@@ -566,6 +575,31 @@ int ce_get_fields(ce_sim* s, double* f, double* v, int mode, ce_scalars_t* sc) {
 int64_t ce_device_bytes(const ce_sim* s) { return s ? s->bytes : 0; }
 
 int ce_kernel_in_use(const ce_sim* s) { return s ? s->kernel : CE_KERNEL_GENERIC; }
+
+int ce_replan(ce_sim* s, int rows, int stages, int zchunks) {
+  g_err.clear();
+  int rc = check_sim(s, "ce_replan");
+  if (rc) return rc;
+  if (s->batch) return fail(CE_ESTATE, "ce_replan: the handle is a member of a batch");
+  if (s->kernel != CE_KERNEL_SWEEP) return fail(CE_EINVAL, "ce_replan: this handle runs the generic kernel");
+  if ((rows != 0 && rows != 4 && rows != 8 && rows != 16) || (stages != 0 && (stages < 3 || stages > 5)) || zchunks < 0 ||
+      zchunks > s->N / 2 || !ce::sweep_hint_valid(s->N, s->nf, s->prec, rows, stages))
+    return fail(CE_EINVAL, "ce_replan: no compiled z-sweep variant matches");
+  if ((rc = select_device(s))) return rc;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_replan");
+  ce::SweepPlan p{};
+  e = ce::sweep_prepare(p, s->f, s->w, s->N, s->nf, s->prec, s->device, rows, stages, zchunks);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_replan: plan");
+  for (auto& g : s->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  s->graphs_ok = true;
+  s->plan = p;
+  return CE_OK;
+}
 
 int ce_sweep_plan(const ce_sim* s, int* rows, int* stages, int* zchunks) {
   if (!s || !rows || !stages || !zchunks) return fail(CE_EINVAL, "ce_sweep_plan: NULL argument");

@@ -79,6 +79,8 @@ struct StepArgs {
   double half_inv_dx2;
   int update_scalars;   // 1: reduce G, V and advance a, a', a'' in the last block
   int in_slot;          // which ping-pong buffer set is the input (selects TMA maps)
+  long long wait_cycles;      // bound of every mbarrier wait (SM clock cycles)
+  unsigned int missing_tx;    // test-only: bytes announced per plane that never arrive
   const DevScalars* sc_in;
   DevScalars* sc_out;
   double* partials;     // >= 2 * number of blocks

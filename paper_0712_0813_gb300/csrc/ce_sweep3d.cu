@@ -48,7 +48,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
 
 // Default variant when the caller gives no hint: the first that applies in
 // this order of preference.
-constexpr int kPreference[] = {0, 1, 3, 2};
+constexpr int kPreference[] = {0, 1, 3, 2, 4, 5};
 
 }  // namespace
 

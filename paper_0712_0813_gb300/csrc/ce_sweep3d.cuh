@@ -46,23 +46,29 @@ struct Variant {
   int ty;
   int stages;
 };
-constexpr Variant kVariants[] = {{8, 4}, {8, 5}, {16, 3}, {16, 4}};
+constexpr Variant kVariants[] = {{8, 4}, {8, 5}, {16, 3}, {16, 4}, {4, 4}, {4, 5}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// Bytes of one x-halo column buffer (TY rows of 16 bytes), padded to the
+// 128-byte alignment every TMA destination needs.
+__host__ __device__ constexpr size_t halo_bytes(int ty) { return ((size_t)ty * 16 + 127) / 128 * 128; }
 
 template <typename T>
 constexpr size_t smem_bytes(int nf, int ty, int stages) {
-  return (size_t)stages * nf * 2 * ((ty + 2) * (32 * (16 / sizeof(T))) + 2 * ty * (16 / sizeof(T))) * sizeof(T) +
+  return (size_t)stages * nf * 2 * ((ty + 2) * (32 * (16 / sizeof(T))) * sizeof(T) + 2 * halo_bytes(ty)) +
          2 * stages * sizeof(uint64_t) + 128;
 }
 
-// Resident CTAs per SM the kernel is compiled for (register budget).
+// Resident CTAs per SM the kernel is compiled for (register budget): as many
+// as shared memory admits, up to 2 for 8-row tiles and 4 for 4-row tiles.
 template <typename T, int NF, int TY, int NST>
 constexpr int min_blocks() {
-  return (TY <= 8 && 2 * smem_bytes<T>(NF, TY, NST) <= 220 * 1024) ? 2 : 1;
+  constexpr size_t by_smem = (220 * 1024) / smem_bytes<T>(NF, TY, NST);
+  constexpr int cap = TY <= 4 ? 4 : (TY <= 8 ? 2 : 1);
+  return by_smem < 1 ? 1 : (by_smem < (size_t)cap ? (int)by_smem : cap);
 }
 
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -135,8 +141,9 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
   constexpr int TX = 32 * VX;            // tile width: one warp per row
   constexpr int H = VX;                  // x-halo box width (16 bytes)
   constexpr int MAIN = (TY + 2) * TX;    // tile + y-halo rows, elements
-  constexpr int ARR = MAIN + 2 * TY * H; // + left and right x-halo columns
-  constexpr uint32_t kPlaneBytes = 2u * NF * ARR * sizeof(T);
+  constexpr int HALO = (int)(halo_bytes(TY) / sizeof(T));  // one x-halo column buffer, elements
+  constexpr int ARR = MAIN + 2 * HALO;   // + left and right x-halo columns
+  constexpr uint32_t kPlaneBytes = 2u * NF * (MAIN + 2 * TY * H) * sizeof(T);  // bytes TMA delivers per plane
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   // TMA destinations are kept 128-byte aligned whatever the static smem layout.
   unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
       if (*(volatile int*)&s_abort) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > p.wait_cycles) {
         atomicExch(&s_abort, 1);
         atomicCAS(p.status, CE_OK, CE_ETIMEOUT);
         return false;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
         if (pidx >= NST && !wait_bar(&empty[slot], (uint32_t)(pidx / NST - 1) & 1u)) break;
         int zz = plane_z(pidx);
         zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
-        mbar_expect_tx(&full[slot], kPlaneBytes);
+        mbar_expect_tx(&full[slot], kPlaneBytes + p.missing_tx);
 #pragma unroll
         for (int i = 0; i < NF; ++i) {
 #pragma unroll
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
               tma_load_3d(dst, &maps.m[i][a][0], x0, y0 - 1, zz, &full[slot]);
             }
             tma_load_3d(dst + MAIN, &maps.m[i][a][3], xl, y0, zz, &full[slot]);
-            tma_load_3d(dst + MAIN + TY * H, &maps.m[i][a][3], xr, y0, zz, &full[slot]);
+            tma_load_3d(dst + MAIN + HALO, &maps.m[i][a][3], xr, y0, zz, &full[slot]);
           }
         }
         issued = pidx + 1;
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
           for (int j = 0; j < VX; ++j) yp[j] = fmaT(dd, fmaT(c, f[j], w[j]), f[j]);
         }
         // x neighbours: adjacent lanes; the row ends read the TMA'd halo columns
-        const int hoff = (lane == 0) ? MAIN + r * H + (H - 1) : MAIN + TY * H + r * H;
+        const int hoff = (lane == 0) ? MAIN + r * H + (H - 1) : MAIN + HALO + r * H;
         const T hf = cf[hoff], hw = cw[hoff];
         const T gh = fmaT(dd, fmaT(c, hf, hw), hf);
         T gl = __shfl_up_sync(0xffffffffu, gc[i][VX - 1], 1);
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
     if (threadIdx.x == TY * 32) {
       for (int k = s_min_waited; k < issued; ++k) {
         const long long t0 = clock64();
-        while (!mbar_try_wait(&full[k % NST], (uint32_t)(k / NST) & 1u) && clock64() - t0 < kWaitCycles) {
+        while (!mbar_try_wait(&full[k % NST], (uint32_t)(k / NST) & 1u) && clock64() - t0 < p.wait_cycles) {
         }
       }
     }

@@ -7,6 +7,8 @@ namespace ce {
 namespace sweep {
 namespace {
 
+static_assert(kNumVariants == 6, "the switches below cover every compiled variant");
+
 template <int NF, int V>
 cudaError_t launch_v(const StepArgs<float>& a, const SweepMaps& m, dim3 grid, size_t smem, cudaStream_t st) {
   constexpr int TY = kVariants[V].ty, NST = kVariants[V].stages;
@@ -26,7 +28,9 @@ cudaError_t launch_nf(int v, const StepArgs<float>& a, const SweepMaps& m, dim3 
     case 0: return launch_v<NF, 0>(a, m, g, smem, st);
     case 1: return launch_v<NF, 1>(a, m, g, smem, st);
     case 2: return launch_v<NF, 2>(a, m, g, smem, st);
-    default: return launch_v<NF, 3>(a, m, g, smem, st);
+    case 3: return launch_v<NF, 3>(a, m, g, smem, st);
+    case 4: return launch_v<NF, 4>(a, m, g, smem, st);
+    default: return launch_v<NF, 5>(a, m, g, smem, st);
   }
 }
 
@@ -36,7 +40,9 @@ const void* kptr_nf(int v) {
     case 0: return kptr_v<NF, 0>();
     case 1: return kptr_v<NF, 1>();
     case 2: return kptr_v<NF, 2>();
-    default: return kptr_v<NF, 3>();
+    case 3: return kptr_v<NF, 3>();
+    case 4: return kptr_v<NF, 4>();
+    default: return kptr_v<NF, 5>();
   }
 }
 

@@ -62,6 +62,7 @@ BAD = [
     (dict(dims=3, N=1 << 12), "2^34"),
     (dict(dims=2, N=100, kernel="sweep"), "z-sweep"),
     (dict(tile_rows=12), "tile_rows"),
+    (dict(tile_rows=2), "tile_rows"),
     (dict(stages=9), "stages"),
     (dict(zchunks=-1), "zchunks"),
     (dict(N=16, zchunks=9), "zchunks"),
@@ -111,3 +112,11 @@ def test_batch_rejects_bad_arguments_without_device(capi):
     assert lib.ce_batch_create(None, 0, 0, None, ctypes.byref(out)) == capi.CE_EINVAL
     assert lib.ce_batch_step(None, 1) == capi.CE_EINVAL
     lib.ce_batch_free(None)
+
+
+def test_replan_and_plan_reject_null(capi):
+    lib = capi.load()
+    assert lib.ce_replan(None, 0, 0, 0) == capi.CE_EINVAL
+    import ctypes
+    r = ctypes.c_int()
+    assert lib.ce_sweep_plan(None, ctypes.byref(r), ctypes.byref(r), ctypes.byref(r)) == capi.CE_EINVAL

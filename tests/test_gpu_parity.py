@@ -248,7 +248,7 @@ def test_full_size_256cube_one_step_against_oracle(gpu_capi, orc, precision, tol
     assert abs(sc1.ap_half - st.scale.ap) <= 1e-9 * abs(st.scale.ap)
 
 
-VARIANTS = [(8, 4), (8, 5), (16, 3), (16, 4)]
+VARIANTS = [(8, 4), (8, 5), (16, 3), (16, 4), (4, 4), (4, 5)]
 
 
 @pytest.mark.parametrize("rows,stages", VARIANTS)
