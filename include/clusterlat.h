@@ -197,6 +197,26 @@ int ce_sweep_plan(const ce_sim* sim, int* rows, int* stages, int* zchunks);
  * handle, or no compiled variant matches), CE_ESTATE (member of a batch). */
 int ce_replan(ce_sim* sim, int rows, int stages, int zchunks);
 
+/* Binned power spectrum of field `field` at the current integer time.
+ * With the unnormalised DFT fhat(n) = sum_x f(x) exp(-2 pi i n.x / N) over the
+ * integer modes n (components in (-N/2, N/2]), bin b collects the modes with
+ * floor(|n| + 1/2) = b: power[b] = mean of |fhat(n)|^2 over the bin, count[b]
+ * = number of modes, k[b] = 2 pi b / L.  The mean field lands in bin 0.
+ * (Sec. II: spectra are among the program's outputs; the definition is a
+ * convention.)  Host arrays of nbins doubles; 1 <= nbins <= ceil(sqrt(dims)
+ * N/2) + 2.  The first call allocates a cuFFT plan and work buffers, kept by
+ * the handle.  Synchronises.  Errors: CE_EINVAL, CE_ESTATE, CE_ENOMEM, CE_ECUDA. */
+int ce_spectrum(ce_sim* sim, int field, int nbins, double* k, double* power, double* count);
+
+/* Grid image (Sec. II: a complete state from which a run can be resumed).
+ * ce_save writes a header (lattice, model, a, a'(t+dt/2), a'', t, step) and
+ * f(t), f'(t+dt/2) as float64; ce_load restores it into a handle created with
+ * the same dims, N, L, dt, fields, couplings and expansion, so that the
+ * continuation is bit-identical to an uninterrupted run.  Both synchronise.
+ * Errors: CE_EINVAL (I/O failure, not an image, mismatched lattice), CE_ESTATE. */
+int ce_save(ce_sim* sim, const char* path);
+int ce_load(ce_sim* sim, const char* path);
+
 /* ---- batches: many lattices, one persistent launch per step ------------
  * A batch groups existing handles (any mix of dimensions and sizes, same
  * precision and number of fields, fields already set) and advances all of

@@ -13,7 +13,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                          limit against a cosmic-time RK4 of the physical
                          Klein-Gordon + Friedmann system, energy and Friedmann
                          constraint drift O(dt^2), time reversibility
-  orc_energy/orc_means_variances pinned: numpy definitions, Parseval
+  orc_energy/orc_means_variances pinned: numpy definitions
+  spectrum (numpy FFT + binning) pinned: Parseval, plane-wave and constant fields
   start-up conventions (a(0)=1, u-velocity, kappa default), the IC recipe and the
   Courant rule are conventions the paper leaves open: parity unpinned there.
 """
@@ -220,3 +221,26 @@ def means_variances(p: Params, f: np.ndarray):
     var = np.zeros(p.nf)
     _load().orc_means_variances(ctypes.byref(p.model()), _ptr(f), _ptr(mean), _ptr(var))
     return mean, var
+
+
+def spectrum(p: Params, f_field: np.ndarray, nbins: int):
+    """Binned power spectrum of one field (the library's output definition):
+    fhat(n) = sum_x f(x) exp(-2 pi i n.x / N) (unnormalised DFT, numpy's FFT as
+    the transform), bin b = floor(|n| + 1/2) over the integer modes n with
+    components in (-N/2, N/2]; power[b] = mean |fhat|^2 over the bin,
+    count[b] = number of modes, k[b] = 2 pi b / L.  Parity pinned by Parseval and
+    plane waves (tests); the binning convention itself is not from the paper."""
+    shape = (p.N,) * p.dims
+    F = np.fft.fftn(np.asarray(f_field, dtype=np.float64).reshape(shape))
+    freqs = np.meshgrid(*([np.fft.fftfreq(p.N, 1.0 / p.N)] * p.dims), indexing="ij")
+    nabs = np.sqrt(sum(g * g for g in freqs))
+    bins = np.floor(nabs + 0.5).astype(np.int64).reshape(-1)
+    pw = (np.abs(F) ** 2).reshape(-1)
+    power = np.zeros(nbins)
+    count = np.zeros(nbins)
+    for b, w in zip(bins, pw):
+        if b < nbins:
+            power[b] += w
+            count[b] += 1
+    mean = np.where(count > 0, power / np.maximum(count, 1), 0.0)
+    return 2 * np.pi * np.arange(nbins) / p.L, mean, count

@@ -61,6 +61,7 @@ _keepalive: dict = {}   # handle -> (config, ctypes callbacks, allocation table)
 EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_variances",
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
            "ce_kernel_in_use", "ce_sweep_plan", "ce_replan", "ce_version", "ce_moments_noalloc",
+           "ce_spectrum", "ce_save", "ce_load",
            "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_info", "ce_batch_free")
 
 
@@ -95,6 +96,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_kernel_in_use": (ctypes.c_int, [vp]),
         "ce_sweep_plan": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "ce_replan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "ce_spectrum": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, pd, pd, pd]),
+        "ce_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "ce_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "ce_version": (ctypes.c_int, []),
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
         "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, vp, P(vp)]),
@@ -240,6 +244,21 @@ def ce_sweep_plan(sim):
     return r.value, st.value, z.value
 
 
+def ce_spectrum(sim, field: int, nbins: int):
+    """(k, power, count) arrays of the binned power spectrum of one field."""
+    k, p, n = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
+    _check(load().ce_spectrum(sim, int(field), int(nbins), _dptr(k), _dptr(p), _dptr(n)))
+    return k, p, n
+
+
+def ce_save(sim, path: str):
+    _check(load().ce_save(sim, os.fsencode(path)))
+
+
+def ce_load(sim, path: str):
+    _check(load().ce_load(sim, os.fsencode(path)))
+
+
 def ce_replan(sim, rows: int = 0, stages: int = 0, zchunks: int = 0):
     _check(load().ce_replan(sim, int(rows), int(stages), int(zchunks)))
 
@@ -362,6 +381,15 @@ class Simulation:
 
     def replan(self, rows: int = 0, stages: int = 0, zchunks: int = 0):
         ce_replan(self.handle, rows, stages, zchunks)
+
+    def spectrum(self, field: int, nbins: int):
+        return ce_spectrum(self.handle, field, nbins)
+
+    def save(self, path: str):
+        ce_save(self.handle, path)
+
+    def load(self, path: str):
+        ce_load(self.handle, path)
 
     def close(self):
         if self.handle is not None:

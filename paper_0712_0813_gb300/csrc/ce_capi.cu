@@ -381,6 +381,7 @@ void ce_free(ce_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (auto& g : s->graph)
     if (g) cudaGraphExecDestroy(g);
+  ce::outputs_release(s);
   release_all(s);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;

@@ -206,6 +206,8 @@ void set_last_error(const std::string& msg);
 cudaError_t batch_wait(ce_batch* b);
 // A member is being freed: finish the batch's work and mark the batch unusable.
 void batch_detach(ce_batch* b, ce_sim* s);
+// Release the output work buffers (spectrum plan, arrays) of a handle.
+void outputs_release(const ce_sim* s);
 
 constexpr int kGenericThreads = 256;
 int generic_blocks(int64_t S);

@@ -334,3 +334,32 @@ def test_time_reversibility(orc):
     np.testing.assert_allclose(st.v, -v_before, rtol=0, atol=1e-10)
     assert st.scale.a == pytest.approx(1.0, abs=1e-12)
     assert st.scale.ap == pytest.approx(-(start.scale.ap - dt * start.scale.app), abs=1e-11)
+
+
+# ---------------------------------------------------------------- power spectrum
+
+@pytest.mark.parametrize("dims,N", [(1, 32), (2, 16), (3, 8)])
+def test_spectrum_parseval_and_counts(orc, dims, N):
+    rng = np.random.default_rng(dims)
+    p = orc.Params(dims=dims, N=N, L=5.0, dt=0.01, nf=1)
+    f = rng.standard_normal(N ** dims)
+    nb = int(np.ceil(np.sqrt(dims) * N / 2)) + 2
+    k, power, count = orc.spectrum(p, f, nb)
+    assert count.sum() == N ** dims                       # every mode binned once
+    assert (power * count).sum() == pytest.approx(N ** dims * (f * f).sum(), rel=1e-12)   # Parseval
+    assert k[1] == pytest.approx(2 * np.pi / 5.0)
+
+
+def test_spectrum_plane_wave_and_constant(orc):
+    dims, N, L, A = 3, 16, 4.0, 0.7
+    p = orc.Params(dims=dims, N=N, L=L, dt=0.01, nf=1)
+    X = coords(dims, N, L)
+    n0 = (3, 0, 4)                                         # |n0| = 5
+    f = (A * np.cos(sum(2 * np.pi * nd / L * Xd for nd, Xd in zip(n0, X)))).reshape(-1)
+    k, power, count = orc.spectrum(p, f, 12)
+    S = N ** dims
+    # fhat = A S / 2 at +n0 and -n0, zero elsewhere
+    assert power[5] * count[5] == pytest.approx(2 * (A * S / 2) ** 2, rel=1e-12)
+    assert np.delete(power * count, 5).max() < 1e-18 * power[5] * count[5]
+    k, power, count = orc.spectrum(p, np.full(S, 1.5), 12)
+    assert power[0] == pytest.approx((1.5 * S) ** 2) and count[0] == 1
