@@ -240,7 +240,7 @@ def batched_leg(capi, torch, steps: int, warmup: int, seq_steps: int, hbm_peak: 
         sims.append(sim)
     from paper_0712_0813_gb300 import autotune
     tune = autotune.autotune_batch(sims, stream=stream)   # outside the timed region
-    b = capi.Batch(sims, sweep_len=tune["sweep_len"], stream=stream.cuda_stream)
+    b = capi.Batch(sims, sweep_len=tune["sweep_len"], stream=stream.cuda_stream, ctas_per_sm=tune["ctas_per_sm"])
     info = b.info
     b.step(warmup)
     b.synchronize()
@@ -278,7 +278,7 @@ def batched_leg(capi, torch, steps: int, warmup: int, seq_steps: int, hbm_peak: 
     return {"workload": "96 lattices: 32 x 1D 65536, 32 x 2D 1024^2, 32 x 3D side in {64..192}; 2 fields, "
                         "per-lattice q, phi0, Courant dt, expansion on half",
             "sites": total, "steps": steps, "ms_per_step": ms / steps, "items": info["items"],
-            "sweep_len": tune["sweep_len"], "autotune": tune["table"],
+            "sweep_len": tune["sweep_len"], "ctas_per_sm": tune["ctas_per_sm"], "autotune": tune["table"],
             "blocks": info["blocks"], "value_f32_batched": batched, "fp64_plain_sequential": fp64_seq,
             "f32_plain_sequential": f32_seq, "batched_over_fp64_plain": batched / fp64_seq,
             "sequential_steps": seq_steps,

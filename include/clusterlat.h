@@ -231,12 +231,14 @@ int ce_load(ce_sim* sim, const char* path);
  * results (its items and their summation order do not depend on the mix). */
 typedef struct ce_batch ce_batch;
 
-/* sims: n handles; sweep_len: sites per item along the sweep axis (0 = 32);
- * stream: cudaStream_t for the batch's work (NULL = its own stream).
+/* sims: n handles; sweep_len: sites per item along the sweep axis (0 = 128);
+ * ctas_per_sm: cap on the persistent kernel's resident CTAs per SM, 0..8
+ * (0 = as many as fit); stream: cudaStream_t for the batch's work (NULL = its
+ * own stream).
  * Errors: CE_EINVAL (mixed precision or field count, N not a multiple of 4
  * (FP32) / 2 (FP64), duplicates), CE_ESTATE (a member without fields or
  * already in a batch), CE_ECUDA. */
-int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, void* stream, ce_batch** out);
+int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, int ctas_per_sm, void* stream, ce_batch** out);
 
 /* Advance every member by n >= 0 steps (asynchronous, CUDA graphs of 32). */
 int ce_batch_step(ce_batch* b, int64_t n);

@@ -103,25 +103,27 @@ def load(path: str):
             _cache[k] = TuneResult(v["tile_rows"], v["stages"], v["zchunks"], v["ms_per_step"])
 
 
-def autotune_batch(sims, *, candidates=(16, 32, 64, 128), steps: int = 20, warmup: int = 4,
-                   stream=None) -> dict:
+def autotune_batch(sims, *, candidates=(32, 64, 128, 256), occupancies=(0,), steps: int = 20,
+                   warmup: int = 4, stream=None) -> dict:
     """Pick the batched kernel's item length (sites per item along the sweep
-    axis) for a given set of handles: each candidate batch is timed for `steps`
-    steps with CUDA events (the members' states advance; callers tune on a
-    scratch copy or accept the extra steps)."""
+    axis) and, optionally, a cap on resident CTAs per SM for a set of handles:
+    each candidate batch is timed for `steps` steps with CUDA events (the
+    members' states advance; callers tune on a scratch copy or accept the
+    extra steps)."""
     import torch
     st = torch.cuda.Stream() if stream is None else stream
     table = []
-    for L in candidates:
-        with capi.Batch(sims, sweep_len=L, stream=st.cuda_stream) as b:
-            b.step(warmup)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            b.step(steps)
-            e1.record(st)
-            e1.synchronize()
-            b.synchronize()
-            table.append((L, e0.elapsed_time(e1) / steps))
-    best = min(table, key=lambda t: t[1])
-    return {"sweep_len": best[0], "ms_per_step": best[1], "table": table}
+    for occ in occupancies:
+        for L in candidates:
+            with capi.Batch(sims, sweep_len=L, stream=st.cuda_stream, ctas_per_sm=occ) as b:
+                b.step(warmup)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                b.step(steps)
+                e1.record(st)
+                e1.synchronize()
+                b.synchronize()
+                table.append((L, occ, e0.elapsed_time(e1) / steps))
+    best = min(table, key=lambda t: t[2])
+    return {"sweep_len": best[0], "ctas_per_sm": best[1], "ms_per_step": best[2], "table": table}

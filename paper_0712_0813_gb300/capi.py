@@ -101,7 +101,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "ce_version": (ctypes.c_int, []),
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
-        "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, vp, P(vp)]),
+        "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, P(vp)]),
         "ce_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "ce_batch_synchronize": (ctypes.c_int, [vp]),
         "ce_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
@@ -278,13 +278,13 @@ def ce_moments_noalloc(f_ptr: int, precision: int, n: int, nfields: int, stream:
                                      ctypes.c_void_p(int(mean_ptr)), ctypes.c_void_p(int(var_ptr))))
 
 
-def ce_batch_create(sims, sweep_len: int = 0, stream=None):
+def ce_batch_create(sims, sweep_len: int = 0, stream=None, ctas_per_sm: int = 0):
     """Group handles (ctypes handles or Simulation objects) into a batch."""
     hs = [x.handle if isinstance(x, Simulation) else x for x in sims]
     arr = (ctypes.c_void_p * len(hs))(*[h.value for h in hs])
     b = ctypes.c_void_p()
-    _check(load().ce_batch_create(arr, len(hs), int(sweep_len), ctypes.c_void_p(int(stream) if stream else 0),
-                                  ctypes.byref(b)))
+    _check(load().ce_batch_create(arr, len(hs), int(sweep_len), int(ctas_per_sm),
+                                  ctypes.c_void_p(int(stream) if stream else 0), ctypes.byref(b)))
     return b
 
 
@@ -310,9 +310,9 @@ def ce_batch_free(b):
 class Batch:
     """Owning wrapper around a batch: ``with Batch(sims) as b: b.step(n)``."""
 
-    def __init__(self, sims, sweep_len: int = 0, stream=None):
+    def __init__(self, sims, sweep_len: int = 0, stream=None, ctas_per_sm: int = 0):
         self.sims = list(sims)
-        self.handle = ce_batch_create(self.sims, sweep_len, stream)
+        self.handle = ce_batch_create(self.sims, sweep_len, stream, ctas_per_sm)
 
     def step(self, n):
         ce_batch_step(self.handle, n)

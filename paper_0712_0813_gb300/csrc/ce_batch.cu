@@ -60,17 +60,6 @@ struct BItem {
 };
 
 template <typename T, int VX>
-__device__ __forceinline__ void ld16(const T* p, T (&o)[VX]) {
-  if constexpr (sizeof(T) == 4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  } else {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    o[0] = v.x; o[1] = v.y;
-  }
-}
-
-template <typename T, int VX>
 __device__ __forceinline__ void st16(T* p, const T (&o)[VX]) {
   if constexpr (sizeof(T) == 4) {
     __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
@@ -79,169 +68,276 @@ __device__ __forceinline__ void st16(T* p, const T (&o)[VX]) {
   }
 }
 
-// One warp's row segment of an item.  DIMS 3: row y, sweep z.  DIMS 2: sweep
-// y.  DIMS 1: a single "plane".
-template <typename T, int NF, int DIMS>
-__device__ __forceinline__ void warp_segment(const BMember<T>* __restrict__ m, int in, int x0, int y, int s0,
-                                             int s1, int lane, T& g2loc, T& vloc) {
-  constexpr int VX = 16 / sizeof(T);
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Asynchronous global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_small(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)),
+               "l"(__cvta_generic_to_global(src)), "n"(BYTES)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int PENDING>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+template <typename T, int VX>
+__device__ __forceinline__ void lds16(const T* p, T (&o)[VX]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+}
+
+// Shared-memory layout of one array (f or w of one field) in one ring stage:
+// 10 rows of one segment width (3D: the item's rows plus the two y-halo rows;
+// 2D/1D: row 0 holds the 8 warps' segments side by side), then 16 halo
+// elements (3D: left/right x-neighbours of each row; 2D/1D: of the span).
+template <typename T>
+struct Stage {
+  static constexpr int VX = 16 / sizeof(T);
+  static constexpr int SEG = 32 * VX;
+  static constexpr int ARR = 10 * SEG + 16;
+};
+
+template <typename T, int NF, int NST>
+constexpr size_t batch_smem() {
+  return (size_t)NST * NF * 2 * Stage<T>::ARR * sizeof(T);
+}
+
+// One item, processed by the whole CTA: a cp.async ring of NST stages keeps up
+// to NST - 2 planes in flight while one is computed; one block barrier per plane
+// both publishes the landed plane and frees the slot read two planes earlier.
+// DIMS 3: warp w owns row y0 + w of a 32 x VX segment and sweeps z; DIMS 2: warp
+// w owns segment w of an 8-segment span of one row and sweeps y; DIMS 1: the
+// same span, one "plane".
+template <typename T, int NF, int NST, int DIMS>
+__device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int in, const BItem& it, T* smem,
+                                         int warp, int lane, T& g2loc, T& vloc) {
+  constexpr int VX = Stage<T>::VX, SEG = Stage<T>::SEG, ARR = Stage<T>::ARR;
   const int N = m->N;
   const int64_t NN = (int64_t)N * N;
-  const int nvl = min(32, (N - x0) / VX);  // valid lanes of this segment
-  const bool valid = lane < nvl;
-  const int col = x0 + lane * VX;
-  const int xl = (x0 == 0) ? N - 1 : x0 - 1;
-  const int xr = (x0 + nvl * VX == N) ? 0 : x0 + nvl * VX;
-  const bool need_l = (lane == 0), need_r = (lane == nvl - 1);
-  const int64_t sweep_stride = DIMS == 3 ? NN : (DIMS == 2 ? (int64_t)N : 0);
-  const int64_t row_base = DIMS == 3 ? (int64_t)y * N : 0;
-  const int64_t ym_base = DIMS == 3 ? (int64_t)(y == 0 ? N - 1 : y - 1) * N : 0;
-  const int64_t yp_base = DIMS == 3 ? (int64_t)(y == N - 1 ? 0 : y + 1) * N : 0;
+  // geometry of this warp
+  int x0, nvl, nrows = 8;
+  bool wvalid;
+  if constexpr (DIMS == 3) {
+    nrows = min(8, N - it.y0);
+    wvalid = warp < nrows;
+    x0 = it.x0;
+    nvl = min(32, (N - x0) / VX);
+  } else {
+    x0 = it.x0 + warp * SEG;
+    wvalid = x0 < N;
+    nvl = wvalid ? min(32, (N - x0) / VX) : 0;
+  }
+  const bool valid = wvalid && lane < nvl;
+  const int col = lane * VX;                     // column inside the warp's segment
+  const int span_end = min(N, it.x0 + 8 * SEG);  // 2D/1D: end of the CTA's span
+  const int last_warp = (span_end - it.x0 + SEG - 1) / SEG - 1;
+  const int y = it.y0 + warp;                    // 3D row
+  const auto wrap = [&](int v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
+  const int n = DIMS == 1 ? 1 : it.s1 - it.s0 + 2;
+  const auto plane = [&](int j) { return DIMS == 1 ? 0 : wrap(it.s0 - 1 + j); };
   const T c = (T)m->slot[in].c;
   const T dd = m->dt, kk = m->dt, idx2 = m->inv_dx2;
   T q[3] = {m->q[0], m->q[1], m->q[2]};
-  const T* fi[NF];
-  const T* wi[NF];
-  T* fo[NF];
-  T* wo[NF];
-#pragma unroll
-  for (int i = 0; i < NF; ++i) {
-    fi[i] = m->f[in][i];
-    wi[i] = m->w[in][i];
-    fo[i] = m->f[in ^ 1][i];
-    wo[i] = m->w[in ^ 1][i];
-  }
-  auto wrap = [&](int s) { return s < 0 ? s + N : (s >= N ? s - N : s); };
-  auto own = [&](int s, T (&f)[NF][VX], T (&w)[NF][VX]) {
-    const int64_t o = row_base + (int64_t)wrap(s) * sweep_stride + col;
+  const auto sbuf = [&](int slot, int i, int a) { return smem + ((size_t)(slot * NF + i) * 2 + a) * ARR; };
+
+  const auto issue = [&](int j) {
+    const int slot = j % NST;
+    const int64_t poff = DIMS == 3 ? (int64_t)plane(j) * NN : (DIMS == 2 ? (int64_t)plane(j) * N : 0);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
-      if (valid) {
-        ld16<T, VX>(fi[i] + o, f[i]);
-        ld16<T, VX>(wi[i] + o, w[i]);
-      } else {
 #pragma unroll
-        for (int j = 0; j < VX; ++j) f[i][j] = w[i][j] = T(0);
+      for (int a = 0; a < 2; ++a) {
+        const T* base = (a ? m->w[in][i] : m->f[in][i]) + poff;
+        T* st = sbuf(slot, i, a);
+        if constexpr (DIMS == 3) {
+          if (valid) cp16(st + (warp + 1) * SEG + col, base + (int64_t)y * N + x0 + col);
+          if (warp == 0 && lane < nvl) cp16(st + col, base + (int64_t)wrap(it.y0 - 1) * N + x0 + col);
+          if (warp == nrows - 1 && lane < nvl)
+            cp16(st + (nrows + 1) * SEG + col, base + (int64_t)wrap(it.y0 + nrows) * N + x0 + col);
+          if (wvalid && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG + 2 * warp, base + (int64_t)y * N + wrap(x0 - 1));
+          if (wvalid && lane == nvl - 1)
+            cp_small<sizeof(T)>(st + 10 * SEG + 2 * warp + 1, base + (int64_t)y * N + wrap(x0 + nvl * VX));
+        } else {
+          if (valid) cp16(st + warp * SEG + col, base + x0 + col);
+          if (warp == 0 && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG, base + wrap(it.x0 - 1));
+          if (warp == last_warp && lane == nvl - 1)
+            cp_small<sizeof(T)>(st + 10 * SEG + 1, base + (span_end == N ? 0 : span_end));
+        }
       }
     }
   };
-  auto gval = [&](T f, T w) { return fmaT(dd, fmaT(c, f, w), f); };
+  const auto gval = [&](T f, T w) { return fmaT(dd, fmaT(c, f, w), f); };
+  const int own_row = DIMS == 3 ? (warp + 1) * SEG + col : warp * SEG + col;
 
-  T gp[NF][VX], gc[NF][VX], vc[NF][VX], pf[NF][VX], pw[NF][VX];
-  if constexpr (DIMS >= 2) {
-    own(s0 - 1, pf, pw);
-#pragma unroll
-    for (int i = 0; i < NF; ++i)
-#pragma unroll
-      for (int j = 0; j < VX; ++j) gp[i][j] = gval(pf[i][j], pw[i][j]);
-  }
-  own(s0, pf, pw);
-#pragma unroll
-  for (int i = 0; i < NF; ++i)
-#pragma unroll
-    for (int j = 0; j < VX; ++j) {
-      vc[i][j] = fmaT(c, pf[i][j], pw[i][j]);
-      gc[i][j] = fmaT(dd, vc[i][j], pf[i][j]);
-    }
-  if constexpr (DIMS >= 2) own(s0 + 1, pf, pw);
-
-  for (int s = s0; s < s1; ++s) {
-    T gn[NF][VX], vn[NF][VX];
-    if constexpr (DIMS >= 2) {
-#pragma unroll
-      for (int i = 0; i < NF; ++i)
-#pragma unroll
-        for (int j = 0; j < VX; ++j) {
-          vn[i][j] = fmaT(c, pf[i][j], pw[i][j]);
-          gn[i][j] = fmaT(dd, vn[i][j], pf[i][j]);
-        }
-      if (s + 2 <= s1) own(s + 2, pf, pw);  // prefetch two planes ahead of s
-    }
-    const int64_t here = row_base + (int64_t)s * sweep_stride;
+  // one plane's update at the own sites from registers (gp, gc, gn) and the
+  // staged current plane (y and x neighbours)
+  T gp[NF][VX], gc[NF][VX], vc[NF][VX];
+  const auto update = [&](int j, const T (&gn)[NF][VX]) {
+    const int slot = j % NST;
+    const int zj = plane(j);
     T lap[NF][VX];
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
+      const T* cf = sbuf(slot, i, 0);
+      const T* cw = sbuf(slot, i, 1);
       T ym[VX], yp[VX];
       if constexpr (DIMS == 3) {
         T f[VX], w[VX];
-        if (valid) {
-          ld16<T, VX>(fi[i] + ym_base + (int64_t)s * NN + col, f);
-          ld16<T, VX>(wi[i] + ym_base + (int64_t)s * NN + col, w);
+        lds16<T, VX>(cf + warp * SEG + col, f);
+        lds16<T, VX>(cw + warp * SEG + col, w);
 #pragma unroll
-          for (int j = 0; j < VX; ++j) ym[j] = gval(f[j], w[j]);
-          ld16<T, VX>(fi[i] + yp_base + (int64_t)s * NN + col, f);
-          ld16<T, VX>(wi[i] + yp_base + (int64_t)s * NN + col, w);
+        for (int k = 0; k < VX; ++k) ym[k] = gval(f[k], w[k]);
+        lds16<T, VX>(cf + (warp + 2) * SEG + col, f);
+        lds16<T, VX>(cw + (warp + 2) * SEG + col, w);
 #pragma unroll
-          for (int j = 0; j < VX; ++j) yp[j] = gval(f[j], w[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < VX; ++j) ym[j] = yp[j] = T(0);
-        }
+        for (int k = 0; k < VX; ++k) yp[k] = gval(f[k], w[k]);
       }
-      const int64_t hrow = row_base + (int64_t)s * sweep_stride;
-      T hlv = T(0), hrv = T(0);
-      if (need_l) hlv = gval(__ldg(fi[i] + hrow + xl), __ldg(wi[i] + hrow + xl));
-      if (need_r) hrv = gval(__ldg(fi[i] + hrow + xr), __ldg(wi[i] + hrow + xr));
+      // x neighbours: adjacent lanes; segment ends from the staged row or the halo
+      T hl, hr;
+      if constexpr (DIMS == 3) {
+        hl = gval(cf[10 * SEG + 2 * warp], cw[10 * SEG + 2 * warp]);
+        hr = gval(cf[10 * SEG + 2 * warp + 1], cw[10 * SEG + 2 * warp + 1]);
+      } else {
+        const int li = warp > 0 ? warp * SEG - 1 : 10 * SEG;
+        const bool inner_r = x0 + nvl * VX < span_end;
+        const int ri = inner_r ? warp * SEG + nvl * VX : 10 * SEG + 1;
+        hl = gval(cf[li], cw[li]);
+        hr = gval(cf[ri], cw[ri]);
+      }
       T gl = __shfl_up_sync(0xffffffffu, gc[i][VX - 1], 1);
       T gr = __shfl_down_sync(0xffffffffu, gc[i][0], 1);
-      if (need_l) gl = hlv;
-      if (need_r) gr = hrv;
+      if (lane == 0) gl = hl;
+      if (lane == nvl - 1) gr = hr;
 #pragma unroll
-      for (int j = 0; j < VX; ++j) {
-        const T g = gc[i][j];
-        const T xm = (j == 0) ? gl : gc[i][j - 1];
-        const T xp = (j == VX - 1) ? gr : gc[i][j + 1];
+      for (int k = 0; k < VX; ++k) {
+        const T g = gc[i][k];
+        const T xm = (k == 0) ? gl : gc[i][k - 1];
+        const T xp = (k == VX - 1) ? gr : gc[i][k + 1];
         T acc = T(0);
         acc += (xp + xm) - T(2) * g;
         T d2 = (xp - g) * (xp - g);
         if constexpr (DIMS == 3) {
-          acc += (yp[j] + ym[j]) - T(2) * g;
-          acc += (gn[i][j] + gp[i][j]) - T(2) * g;
-          d2 = fmaT(yp[j] - g, yp[j] - g, d2);
-          d2 = fmaT(gn[i][j] - g, gn[i][j] - g, d2);
+          acc += (yp[k] + ym[k]) - T(2) * g;
+          acc += (gn[i][k] + gp[i][k]) - T(2) * g;
+          d2 = fmaT(yp[k] - g, yp[k] - g, d2);
+          d2 = fmaT(gn[i][k] - g, gn[i][k] - g, d2);
         } else if constexpr (DIMS == 2) {
-          acc += (gn[i][j] + gp[i][j]) - T(2) * g;
-          d2 = fmaT(gn[i][j] - g, gn[i][j] - g, d2);
+          acc += (gn[i][k] + gp[i][k]) - T(2) * g;
+          d2 = fmaT(gn[i][k] - g, gn[i][k] - g, d2);
         }
-        lap[i][j] = acc * idx2;
+        lap[i][k] = acc * idx2;
         if (valid) g2loc += d2;
       }
     }
 #pragma unroll
-    for (int j = 0; j < VX; ++j) {
+    for (int k = 0; k < VX; ++k) {
       T gs[NF], dv[NF], vs;
 #pragma unroll
-      for (int i = 0; i < NF; ++i) gs[i] = gc[i][j];
+      for (int i = 0; i < NF; ++i) gs[i] = gc[i][k];
       model_dv<T, NF>(gs, q, dv, vs);
       if (valid) vloc += vs;
 #pragma unroll
-      for (int i = 0; i < NF; ++i) lap[i][j] = fmaT(kk, lap[i][j] - dv[i], vc[i][j]);
+      for (int i = 0; i < NF; ++i) lap[i][k] = fmaT(kk, lap[i][k] - dv[i], vc[i][k]);
     }
     if (valid) {
+      const int64_t here = DIMS == 3 ? (int64_t)zj * NN + (int64_t)y * N + x0 + col
+                                     : (DIMS == 2 ? (int64_t)zj * N + x0 + col : (int64_t)x0 + col);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
-        st16<T, VX>(fo[i] + here + col, gc[i]);
-        st16<T, VX>(wo[i] + here + col, lap[i]);
+        st16<T, VX>(m->f[in ^ 1][i] + here, gc[i]);
+        st16<T, VX>(m->w[in ^ 1][i] + here, lap[i]);
       }
     }
-    if constexpr (DIMS >= 2) {
+  };
+  const auto own_g = [&](int j, T (&g)[NF][VX], T (&v)[NF][VX], bool want_v) {
 #pragma unroll
-      for (int i = 0; i < NF; ++i)
+    for (int i = 0; i < NF; ++i) {
+      T f[VX], w[VX];
+      if (valid) {
+        lds16<T, VX>(sbuf(j % NST, i, 0) + own_row, f);
+        lds16<T, VX>(sbuf(j % NST, i, 1) + own_row, w);
+      } else {
 #pragma unroll
-        for (int j = 0; j < VX; ++j) {
-          gp[i][j] = gc[i][j];
-          gc[i][j] = gn[i][j];
-          vc[i][j] = vn[i][j];
-        }
+        for (int k = 0; k < VX; ++k) f[k] = w[k] = T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < VX; ++k) {
+        const T vv = fmaT(c, f[k], w[k]);
+        if (want_v) v[i][k] = vv;
+        g[i][k] = fmaT(dd, vv, f[k]);
+      }
+    }
+  };
+
+  // prologue: fill the ring
+#pragma unroll
+  for (int j = 0; j < NST; ++j) {
+    if (j < n) issue(j);
+    cp_commit();
+  }
+  if constexpr (DIMS == 1) {
+    cp_wait<0>();
+    __syncthreads();
+    T none[NF][VX];
+    if (wvalid) {
+      own_g(0, gc, vc, true);
+      update(0, none);
+    }
+    return;
+  } else {
+    cp_wait<NST - 2>();   // planes 0 and 1 have landed
+    __syncthreads();
+    if (wvalid) {
+      T unused[NF][VX];
+      own_g(0, gp, unused, false);
+      own_g(1, gc, vc, true);
+    }
+    for (int j = 1; j <= n - 2; ++j) {
+      cp_wait<NST - 3>();  // plane j + 1 has landed (own copies) ...
+      __syncthreads();     // ... for every thread, and plane j - 1's slot is free
+      if (j + NST - 1 < n) issue(j + NST - 1);
+      cp_commit();
+      if (wvalid) {
+        T gn[NF][VX], vn[NF][VX];
+        own_g(j + 1, gn, vn, true);
+        update(j, gn);
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+#pragma unroll
+          for (int k = 0; k < VX; ++k) {
+            gp[i][k] = gc[i][k];
+            gc[i][k] = gn[i][k];
+            vc[i][k] = vn[i][k];
+          }
+      }
     }
   }
 }
 
-template <typename T, int NF>
+template <typename T, int NF, int NST>
 __global__ void __launch_bounds__(kThreads) k_step_batched(const BMember<T>* __restrict__ members,
                                                             const BItem* __restrict__ items, int n_items,
                                                             unsigned int* queue, int par) {
-  constexpr int VX = 16 / sizeof(T);
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  T* smem = reinterpret_cast<T*>(smem_dyn);
   __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -253,16 +349,9 @@ __global__ void __launch_bounds__(kThreads) k_step_batched(const BMember<T>* __r
     const BMember<T>* m = members + it.member;
     const int in = m->p0 ^ par;
     T g2loc = T(0), vloc = T(0);
-    if (m->dims == 3) {
-      const int y = it.y0 + warp;
-      if (y < m->N) warp_segment<T, NF, 3>(m, in, it.x0, y, it.s0, it.s1, lane, g2loc, vloc);
-    } else {
-      const int x0 = it.x0 + warp * 32 * VX;
-      if (x0 < m->N) {
-        if (m->dims == 2) warp_segment<T, NF, 2>(m, in, x0, 0, it.s0, it.s1, lane, g2loc, vloc);
-        else warp_segment<T, NF, 1>(m, in, x0, 0, 0, 1, lane, g2loc, vloc);
-      }
-    }
+    if (m->dims == 3) run_item<T, NF, NST, 3>(m, in, it, smem, warp, lane, g2loc, vloc);
+    else if (m->dims == 2) run_item<T, NF, NST, 2>(m, in, it, smem, warp, lane, g2loc, vloc);
+    else run_item<T, NF, NST, 1>(m, in, it, smem, warp, lane, g2loc, vloc);
     if (m->update_scalars) {
       double g2 = (double)g2loc, pot = (double)vloc;
       block_sum2(g2, pot);
@@ -313,6 +402,7 @@ struct ce_batch {
   unsigned int* d_done = nullptr;    // per member
   double* d_partials = nullptr;      // 2 per item
   int n_items = 0, blocks = 0, par = 0, sweep_len = 32;
+  int ctas_per_sm = 0;               // cap on resident CTAs per SM (0: as many as fit)
   int64_t sites = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_ok = true;
@@ -331,11 +421,15 @@ int bcuda(cudaError_t e, const char* what) {
   return CE_ECUDA;
 }
 
+constexpr int kBatchStages = 4;
+
 template <typename T, int NF>
 cudaError_t launch_nf(const ce_batch* b, int par) {
-  ce::k_step_batched<T, NF><<<b->blocks, ce::kThreads, 0, b->stream>>>(
-      static_cast<const ce::BMember<T>*>(b->d_members), static_cast<const ce::BItem*>(b->d_items), b->n_items,
-      b->d_queue, par);
+  const auto* mem = static_cast<const ce::BMember<T>*>(b->d_members);
+  const auto* it = static_cast<const ce::BItem*>(b->d_items);
+  constexpr size_t smem = ce::batch_smem<T, NF, kBatchStages>();
+  ce::k_step_batched<T, NF, kBatchStages><<<b->blocks, ce::kThreads, smem, b->stream>>>(mem, it, b->n_items,
+                                                                                         b->d_queue, par);
   return cudaGetLastError();
 }
 
@@ -353,21 +447,28 @@ cudaError_t launch_batch(const ce_batch* b, int par) {
   return b->prec == CE_F32 ? launch_t<float>(b, par) : launch_t<double>(b, par);
 }
 
-const void* batch_kernel(int prec, int nf) {
-  if (prec == CE_F32) {
-    switch (nf) {
-      case 1: return (const void*)&ce::k_step_batched<float, 1>;
-      case 2: return (const void*)&ce::k_step_batched<float, 2>;
-      case 3: return (const void*)&ce::k_step_batched<float, 3>;
-      default: return (const void*)&ce::k_step_batched<float, 4>;
-    }
-  }
+template <typename T, int NF>
+cudaError_t prepare_nf(int* per_sm) {
+  const void* k = (const void*)&ce::k_step_batched<T, NF, kBatchStages>;
+  constexpr size_t smem = ce::batch_smem<T, NF, kBatchStages>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, ce::kThreads, smem);
+  return e;
+}
+
+template <typename T>
+cudaError_t prepare_t(int nf, int* per_sm) {
   switch (nf) {
-    case 1: return (const void*)&ce::k_step_batched<double, 1>;
-    case 2: return (const void*)&ce::k_step_batched<double, 2>;
-    case 3: return (const void*)&ce::k_step_batched<double, 3>;
-    default: return (const void*)&ce::k_step_batched<double, 4>;
+    case 1: return prepare_nf<T, 1>(per_sm);
+    case 2: return prepare_nf<T, 2>(per_sm);
+    case 3: return prepare_nf<T, 3>(per_sm);
+    default: return prepare_nf<T, 4>(per_sm);
   }
+}
+
+// Raise the kernel's shared-memory limit and report how many CTAs fit an SM.
+cudaError_t batch_prepare(int prec, int nf, int* per_sm) {
+  return prec == CE_F32 ? prepare_t<float>(nf, per_sm) : prepare_t<double>(nf, per_sm);
 }
 
 // Cut every member into items of about kWarps x 32 x VX x sweep_len sites.
@@ -512,12 +613,13 @@ void ce::batch_detach(ce_batch* b, ce_sim* s) {
 
 extern "C" {
 
-int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, void* stream, ce_batch** out) {
+int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, int ctas_per_sm, void* stream, ce_batch** out) {
   ce::set_last_error("");
   if (!out) return bfail(CE_EINVAL, "ce_batch_create: out is NULL");
   *out = nullptr;
   if (!sims || n < 1) return bfail(CE_EINVAL, "ce_batch_create: need at least one simulation");
   if (sweep_len < 0 || sweep_len > 4096) return bfail(CE_EINVAL, "ce_batch_create: sweep_len must be 0..4096");
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return bfail(CE_EINVAL, "ce_batch_create: ctas_per_sm must be 0..8");
   const ce_sim* s0 = sims[0];
   if (!s0) return bfail(CE_EINVAL, "ce_batch_create: NULL member");
   for (int k = 0; k < n; ++k) {
@@ -542,7 +644,8 @@ int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, void* stream, ce_
   b->prec = s0->prec;
   b->nf = s0->nf;
   b->device = s0->device;
-  b->sweep_len = sweep_len > 0 ? sweep_len : 32;
+  b->sweep_len = sweep_len > 0 ? sweep_len : 128;
+  b->ctas_per_sm = ctas_per_sm;
   for (ce_sim* s : b->members) {
     e = cudaStreamSynchronize(s->stream);   // members' own queued work finishes first
     if (e != cudaSuccess) {
@@ -576,9 +679,9 @@ int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, void* stream, ce_
     return rc;
   }
   int per_sm = 0, sms = 0;
-  const void* kern = batch_kernel(b->prec, b->nf);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ce::kThreads, 0);
+  e = batch_prepare(b->prec, b->nf, &per_sm);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess && b->ctas_per_sm > 0) per_sm = std::min(per_sm, b->ctas_per_sm);
   if (e != cudaSuccess || per_sm < 1) {
     release(b);
     delete b;

@@ -109,7 +109,7 @@ def test_batch_rejects_bad_arguments_without_device(capi):
     lib = capi.load()
     import ctypes
     out = ctypes.c_void_p()
-    assert lib.ce_batch_create(None, 0, 0, None, ctypes.byref(out)) == capi.CE_EINVAL
+    assert lib.ce_batch_create(None, 0, 0, 0, None, ctypes.byref(out)) == capi.CE_EINVAL
     assert lib.ce_batch_step(None, 1) == capi.CE_EINVAL
     lib.ce_batch_free(None)
 
