@@ -191,7 +191,7 @@ def time_device_steps(capi, torch, f0, u0, precision, steps, warmup, barrier, sa
     barrier()
     sim.synchronize()  # surfaces any latched device error
     ms = e0.elapsed_time(e1)
-    kernel = {1: "generic", 2: "sweep"}[sim.kernel]
+    kernel = {1: "generic", 2: "sweep", 3: "rows"}[sim.kernel]
     plan = sim.sweep_plan
     sim.close()
     return ms, kernel, clocks, plan

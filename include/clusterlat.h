@@ -72,6 +72,8 @@ extern "C" {
 #define CE_KERNEL_AUTO    0 /* z-sweep kernel where it applies, else generic  */
 #define CE_KERNEL_GENERIC 1 /* one thread per site, any d and N              */
 #define CE_KERNEL_SWEEP   2 /* 3D z-sweep kernel (CE_EINVAL if it does not apply) */
+#define CE_KERNEL_ROWS    3 /* the batched row-sweep kernel on this one lattice:
+                               any d, N a multiple of 4 (FP32) / 2 (FP64)      */
 
 /* ---- config flags ---------------------------------------------------- */
 #define CE_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt < 2/omega_max check       */
@@ -185,7 +187,7 @@ const char* ce_last_error(void);
 /* Bytes of device memory the handle holds (state + scratch). */
 int64_t ce_device_bytes(const ce_sim* sim);
 
-/* Which kernel ce_step launches: CE_KERNEL_GENERIC or CE_KERNEL_SWEEP. */
+/* Which kernel ce_step launches: CE_KERNEL_GENERIC, _SWEEP or _ROWS. */
 int ce_kernel_in_use(const ce_sim* sim);
 
 /* The z-sweep launch plan in use: tile rows, pipeline stages and z-chunks

@@ -603,6 +603,77 @@ void advance_members(ce_batch* b, int64_t steps) {
 
 cudaError_t ce::batch_wait(ce_batch* b) { return b ? cudaStreamSynchronize(b->stream) : cudaSuccess; }
 
+// A private one-lattice batch that lets ce_step run the batched kernel on a
+// single handle (lattices the z-sweep kernel does not cover).  It works on the
+// handle's own stream, with step parity given per launch, and does not make
+// the handle a batch member.
+int ce::rows_create(ce_sim* s, ce_batch** out) {
+  *out = nullptr;
+  ce_batch* b = new (std::nothrow) ce_batch();
+  if (!b) return bfail(CE_ENOMEM, "ce_create: host allocation");
+  b->members.assign(1, s);
+  b->prec = s->prec;
+  b->nf = s->nf;
+  b->device = s->device;
+  b->sweep_len = 128;
+  b->stream = s->stream;
+  b->own_stream = false;
+  b->par = 0;
+  cudaError_t e = cudaMalloc(&b->d_queue, sizeof(unsigned int) * 3);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int) * 3, b->stream);
+  if (e != cudaSuccess) {
+    release(b);
+    delete b;
+    return bcuda(e, "ce_create: row-kernel scratch");
+  }
+  b->d_done = b->d_queue + 2;
+  // item length: the longest (of 128, 64, ..., 4 sites) that still gives two
+  // waves of items, so that one lattice alone fills the GPU
+  int per_sm = 0, sms = 0;
+  e = batch_prepare(b->prec, b->nf, &per_sm);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess || per_sm < 1) {
+    release(b);
+    delete b;
+    return bcuda(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "ce_create: row-kernel occupancy");
+  }
+  {
+    const int64_t N = s->N, seg = 32 * (16 / (int64_t)s->esize);
+    for (int L = 128; L >= 4; L /= 2) {
+      b->sweep_len = L;
+      const int64_t Ls = std::min<int64_t>(L, N);
+      int64_t items;
+      if (s->dims == 3) items = ((N + seg - 1) / seg) * ((N + 7) / 8) * ((N + Ls - 1) / Ls);
+      else if (s->dims == 2) items = ((N + 8 * seg - 1) / (8 * seg)) * ((N + Ls - 1) / Ls);
+      else items = (N + 8 * seg - 1) / (8 * seg);
+      if (items >= 2LL * per_sm * sms) break;
+    }
+  }
+  const int cur = s->cur;
+  s->cur = 0;   // member parity 0: the launch's parity argument is the input buffer set
+  int rc = b->prec == CE_F32 ? upload_tables<float>(b) : upload_tables<double>(b);
+  s->cur = cur;
+  if (rc != CE_OK) {
+    release(b);
+    delete b;
+    return rc;
+  }
+  b->blocks = std::max(1, std::min(per_sm * sms, b->n_items));
+  *out = b;
+  return CE_OK;
+}
+
+cudaError_t ce::rows_launch(const ce_batch* b, int in, cudaStream_t st) {
+  (void)st;   // the private batch was built on the handle's stream
+  return launch_batch(b, in);
+}
+
+void ce::rows_free(ce_batch* b) {
+  if (!b) return;
+  release(b);
+  delete b;
+}
+
 void ce::batch_detach(ce_batch* b, ce_sim* s) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);

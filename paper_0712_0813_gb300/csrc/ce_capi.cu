@@ -80,7 +80,7 @@ int validate(const ce_config* c, int64_t* S_out) {
   for (int i = 0; i + 1 < c->nfields; ++i)
     if (!(c->q[i] >= 0.0) || !std::isfinite(c->q[i])) return fail(CE_EINVAL, "ce_create: q_i must be finite and >= 0");
   if (c->precision != CE_F64 && c->precision != CE_F32) return fail(CE_EINVAL, "ce_create: precision must be CE_F64 or CE_F32");
-  if (c->kernel < CE_KERNEL_AUTO || c->kernel > CE_KERNEL_SWEEP) return fail(CE_EINVAL, "ce_create: unknown kernel");
+  if (c->kernel < CE_KERNEL_AUTO || c->kernel > CE_KERNEL_ROWS) return fail(CE_EINVAL, "ce_create: unknown kernel");
   if (c->expansion != 0 && c->expansion != 1) return fail(CE_EINVAL, "ce_create: expansion must be 0 or 1");
   if (!!c->alloc != !!c->release) return fail(CE_EINVAL, "ce_create: alloc and release hooks go together");
   if (!std::isfinite(c->phi0_over_mpl) || !std::isfinite(c->phi0)) return fail(CE_EINVAL, "ce_create: non-finite phi0");
@@ -141,6 +141,7 @@ ce::StepArgs<T> make_step_args(const ce_sim* s, int in, bool half_kick) {
 
 template <typename T>
 cudaError_t launch_one_step(const ce_sim* s, int in, bool half_kick) {
+  if (s->kernel == CE_KERNEL_ROWS && !half_kick) return ce::rows_launch(s->rows, in, s->stream);
   const ce::StepArgs<T> a = make_step_args<T>(s, in, half_kick);
   if (s->kernel == CE_KERNEL_SWEEP) return ce::launch_step_sweep<T>(a, s->plan, s->stream);
   return ce::launch_step_generic<T>(a, s->generic_blocks, s->stream);
@@ -296,6 +297,9 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
                         ce::sweep_hint_valid(cfg->N, cfg->nfields, cfg->precision, cfg->tile_rows, cfg->stages);
   if (cfg->kernel == CE_KERNEL_SWEEP && !sweep_ok)
     return fail(CE_EINVAL, "ce_create: the z-sweep kernel needs dims == 3 and N a multiple of its tile");
+  const bool rows_ok = cfg->N % (cfg->precision == CE_F32 ? 4 : 2) == 0;
+  if (cfg->kernel == CE_KERNEL_ROWS && !rows_ok)
+    return fail(CE_EINVAL, "ce_create: the row kernel needs N a multiple of 4 (FP32) or 2 (FP64)");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {
@@ -314,7 +318,12 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   s->dx = cfg->L / (double)cfg->N;
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
-  s->kernel = (cfg->kernel == CE_KERNEL_GENERIC || !sweep_ok) ? CE_KERNEL_GENERIC : CE_KERNEL_SWEEP;
+  if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
+  else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
+  else s->kernel = sweep_ok ? CE_KERNEL_SWEEP : CE_KERNEL_GENERIC;
+  // (the row kernel is not an automatic choice: on one lattice alone it measured
+  //  slower than the generic kernel for every shape tried; it pays off across
+  //  the many long items of a batch)
   s->generic_blocks = ce::generic_blocks(S);
   cudaGetDevice(&s->device);
   if (cfg->stream) {
@@ -364,6 +373,13 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
     ce_free(s);
     return fail(CE_ENOMEM, "ce_create: device allocation of scratch failed");
   }
+  if (s->kernel == CE_KERNEL_ROWS) {
+    rc = ce::rows_create(s, &s->rows);
+    if (rc != CE_OK) {
+      ce_free(s);
+      return rc;
+    }
+  }
   e = cudaMemsetAsync(s->aux, 0, sizeof(ce::DevAux), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
@@ -382,6 +398,7 @@ void ce_free(ce_sim* s) {
   for (auto& g : s->graph)
     if (g) cudaGraphExecDestroy(g);
   ce::outputs_release(s);
+  ce::rows_free(s->rows);
   release_all(s);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;

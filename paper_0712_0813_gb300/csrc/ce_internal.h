@@ -190,6 +190,7 @@ struct ce_sim {
   bool graphs_ok = true;
   int64_t bytes = 0;
   ce_batch* batch = nullptr;   // set while the handle is a member of a batch
+  ce_batch* rows = nullptr;    // private one-lattice batch (CE_KERNEL_ROWS)
   struct Alloc {
     void* p;
     size_t n;
@@ -208,6 +209,11 @@ cudaError_t batch_wait(ce_batch* b);
 void batch_detach(ce_batch* b, ce_sim* s);
 // Release the output work buffers (spectrum plan, arrays) of a handle.
 void outputs_release(const ce_sim* s);
+// The batched kernel on one handle (CE_KERNEL_ROWS): build, launch one step
+// reading buffer set `in`, release.
+int rows_create(ce_sim* s, ce_batch** out);
+cudaError_t rows_launch(const ce_batch* b, int in, cudaStream_t st);
+void rows_free(ce_batch* b);
 
 constexpr int kGenericThreads = 256;
 int generic_blocks(int64_t S);

@@ -61,6 +61,7 @@ BAD = [
     (dict(kernel=9), "kernel"),
     (dict(dims=3, N=1 << 12), "2^34"),
     (dict(dims=2, N=100, kernel="sweep"), "z-sweep"),
+    (dict(N=18, precision="f32", kernel="rows"), "row kernel"),
     (dict(tile_rows=12), "tile_rows"),
     (dict(tile_rows=2), "tile_rows"),
     (dict(stages=9), "stages"),

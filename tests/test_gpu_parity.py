@@ -287,3 +287,21 @@ def test_sweep_variants_fp32_vs_oracle(gpu_capi, orc, rows, stages):
         f, v, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
     assert per_field_err(f, ref.f, nf) <= 2e-6
     assert per_field_err(v, ref.v, nf) <= 2e-5
+
+
+@pytest.mark.parametrize("dims,N,precision", [(3, 96, "f64"), (2, 130, "f64"), (1, 2048, "f64"), (3, 40, "f32")])
+def test_row_kernel_single_lattice(gpu_capi, orc, dims, N, precision):
+    """ce_step through the batched row-sweep kernel on one lattice (CE_KERNEL_ROWS,
+    an explicit choice) against the oracle."""
+    q, nf = (1.2,), 2
+    dt = 0.02 if dims > 1 else 0.004
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, 20.0, dt, nf, q, True, 40, precision=precision,
+                                  kernel="rows", amp=1e-2)
+    with sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_ROWS
+        tol_f, tol_v = (TOL64, TOL64) if precision == "f64" else (2e-6, 2e-4)
+        assert per_field_err(f, ref.f, nf) <= tol_f
+        assert per_field_err(v, ref.v, nf) <= tol_v
+    with gpu_capi.Simulation(dims=dims, N=N, L=20.0, dt=dt, nfields=nf, q=q, precision=precision) as auto:
+        assert auto.kernel == (gpu_capi.CE_KERNEL_SWEEP if (dims == 3 and N % (128 if precision == "f32" else 64) == 0)
+                               else gpu_capi.CE_KERNEL_GENERIC)
