@@ -248,6 +248,13 @@ int ce_batch_step(ce_batch* b, int64_t n);
 /* Wait for the batch and report any member's latched device error. */
 int ce_batch_synchronize(ce_batch* b);
 
+/* Per-member status after waiting for the batch: status[k] is CE_OK or the
+ * error member k latched on the device (CE_ENONFINITE, CE_ETIMEOUT).  Members
+ * evolve independently, so a failed member leaves the others' results valid.
+ * status: caller-owned host array of n >= members ints.
+ * Errors: CE_EINVAL (NULL, n too small), CE_ECUDA. */
+int ce_batch_status(ce_batch* b, int* status, int n);
+
 /* Members, work items per step, persistent CTAs, total sites. */
 int ce_batch_info(const ce_batch* b, int* members, int* items, int* blocks, int64_t* sites);
 

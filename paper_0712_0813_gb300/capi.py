@@ -62,7 +62,8 @@ EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
            "ce_kernel_in_use", "ce_sweep_plan", "ce_replan", "ce_version", "ce_moments_noalloc",
            "ce_spectrum", "ce_save", "ce_load",
-           "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_info", "ce_batch_free")
+           "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_status", "ce_batch_info",
+           "ce_batch_free")
 
 
 def lib_path() -> str:
@@ -104,6 +105,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, P(vp)]),
         "ce_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "ce_batch_synchronize": (ctypes.c_int, [vp]),
+        "ce_batch_status": (ctypes.c_int, [vp, P(ctypes.c_int), ctypes.c_int]),
         "ce_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                                          P(ctypes.c_int64)]),
         "ce_batch_free": (None, [vp]),
@@ -297,6 +299,13 @@ def ce_batch_synchronize(b):
     _check(load().ce_batch_synchronize(b))
 
 
+def ce_batch_status(b, n: int) -> list:
+    """Per-member latched status codes (CE_OK = 0) after waiting for the batch."""
+    st = (ctypes.c_int * max(n, 1))()
+    _check(load().ce_batch_status(b, st, int(n)))
+    return [int(st[k]) for k in range(n)]
+
+
 def ce_batch_info(b) -> dict:
     m, it, bl, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
     _check(load().ce_batch_info(b, ctypes.byref(m), ctypes.byref(it), ctypes.byref(bl), ctypes.byref(st)))
@@ -320,6 +329,9 @@ class Batch:
 
     def synchronize(self):
         ce_batch_synchronize(self.handle)
+
+    def member_status(self) -> list:
+        return ce_batch_status(self.handle, len(self.sims))
 
     @property
     def info(self):

@@ -10,11 +10,14 @@
 // about the same size: a CTA of 8 warps takes one item; each warp owns one row
 // segment of 32 lanes x VX consecutive x-sites (VX = 16 B / sizeof(T)) and
 // sweeps it along the slowest axis (z in 3D, y in 2D; 1D items have no sweep).
-// Sweep-axis neighbours stay in registers (own rows are prefetched one plane
-// ahead), x-neighbours come from the adjacent lane by shuffle and from plain
-// loads at the segment ends, the y-neighbour rows of a 3D plane are the
-// neighbouring warps' own rows and are served by L1.  Segments may be partial
-// (N not a multiple of 32 VX): lanes past the row end idle.
+// Each plane of the item (f and w of every field: the 8 rows, in 3D also the
+// two y-halo rows, and the single x-halo elements at the segment ends) is
+// copied into a shared-memory ring with cp.async, so loads in flight hold no
+// registers; one block barrier per plane publishes the landed plane and frees
+// the slot read two planes earlier.  Sweep-axis neighbours stay in registers,
+// x-neighbours come from the adjacent lane by shuffle and from the staged halo
+// elements, y-neighbours from the staged rows.  Segments may be partial (N not a
+// multiple of 32 VX): lanes past the row end idle.
 //
 // The grid is persistent: a fixed number of resident CTAs pull items from one
 // queue (an atomic counter), largest items first.  The CTA that completes the
@@ -803,6 +806,21 @@ int ce_batch_synchronize(ce_batch* b) {
     e = cudaMemcpy(&st, &s->aux->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bcuda(e, "ce_batch_synchronize: status");
     if (st != CE_OK) return bfail(st, "ce_batch_synchronize: a member reported non-finite sums or a timeout");
+  }
+  return CE_OK;
+}
+
+int ce_batch_status(ce_batch* b, int* status, int n) {
+  ce::set_last_error("");
+  if (!b || !status) return bfail(CE_EINVAL, "ce_batch_status: NULL argument");
+  if (n < (int)b->members.size()) return bfail(CE_EINVAL, "ce_batch_status: status array shorter than the batch");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "ce_batch_status");
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    status[k] = CE_OK;
+    if (!b->members[k]) continue;
+    e = cudaMemcpy(&status[k], &b->members[k]->aux->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(e, "ce_batch_status: status");
   }
   return CE_OK;
 }

@@ -96,13 +96,19 @@ def _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac):
     return f, u
 
 
-def courant_dt(dims: int, N: int, L: float, phi0: float, q, cap: float = 0.05) -> float:
+def courant_dt(dims: int, N: int, L: float, phi0: float, q, cap: float = 0.05, amp: float = 1.0) -> float:
     """Time step for configurations that ask for "the Courant limit".
 
-    Convention: omega_max^2 = 4 d / dx^2 + max(3 phi0^2, max_i q_i phi0^2) and
-    dt = min(cap, 0.9 / omega_max), i.e. 45% of the leapfrog bound 2/omega_max.
+    Convention: omega_max^2 = 4 d / dx^2 + max(3 phi_m^2, max_i q_i phi_m^2) and
+    dt = min(cap, 0.9 / omega_max), i.e. 45% of the leapfrog bound 2/omega_max,
+    with the masses taken at phi_m = amp * phi0.  amp = 1 is the start-up value.
+    Strongly coupled lattices (q phi0^2 comparable to 4 d / dx^2) need amp > 1:
+    once the resonance has grown, phi fluctuates locally to several phi0, chi's
+    local mass q phi^2 grows with it, and a step taken at amp = 1 turns the
+    leapfrog unstable at the largest fluctuation.
     """
     dx = L / N
-    m2 = max([3.0 * phi0 * phi0] + [qq * phi0 * phi0 for qq in q])
+    pm = amp * phi0
+    m2 = max([3.0 * pm * pm] + [qq * pm * pm for qq in q])
     w = math.sqrt(4.0 * dims / (dx * dx) + m2)
     return min(cap, 0.9 / w)

@@ -89,6 +89,10 @@ class GpuBackend:
     def wait(self, batch):
         batch.synchronize()
 
+    def member_errors(self, batch) -> dict:
+        """{member index: latched error code} of the members that failed."""
+        return {k: c for k, c in enumerate(batch.member_status()) if c != 0}
+
     def result(self, handle) -> dict:
         en = handle.energy()
         mean, var = handle.means_variances()
@@ -181,7 +185,7 @@ class Server:
         pending = sorted(jobs, key=lambda j: (j.arrival, j.id))
         self._t0 = self.clock()
         batch = None
-        members: set = set()              # ids of the jobs inside the current batch
+        members: list = []                # the jobs inside the current batch, in member order
         dirty = True
         while pending or self.active:
             dirty |= self._admit(pending, self.clock() - self._t0)
@@ -198,10 +202,10 @@ class Server:
                 if batch is not None:
                     self.backend.free_batch(batch)
                 batch = self.backend.make_batch([h for _, h, _ in self.active])
-                members = {j.id for j, _, _ in self.active}
+                members = [j for j, _, _ in self.active]
                 self.rebuilds += 1
                 dirty = False
-            n = min(min(j.steps - j.steps_done for j, _, _ in self.active), self.chunk_steps)
+            n = min(min(j.steps - j.steps_done for j in members), self.chunk_steps)
             try:
                 self.backend.step(batch, n)
                 # arrivals during the chunk are created now: their uploads overlap
@@ -209,23 +213,37 @@ class Server:
                 dirty |= self._admit(pending, self.clock() - self._t0)
                 self.backend.wait(batch)
             except Exception as e:
-                for job, _, _ in self.active:
-                    job.state = "failed"
-                    job.error = f"chunk: {e}"
+                # Members evolve independently: when the batch can say which
+                # members latched an error, only those fail and the others keep
+                # the completed chunk; otherwise the whole chunk fails.
+                bad = self._member_errors(batch)
+                for k, job in enumerate(members):
+                    if bad and k not in bad:
+                        job.steps_done += n
+                    elif job.state == "running":
+                        job.state = "failed"
+                        job.error = f"chunk: {e}" if not bad else f"chunk: member error {bad[k]} ({e})"
                 self.backend.free_batch(batch)
                 batch = None
-                members = set()
-                self._retire(lambda j: False)
+                members = []
+                self._retire(lambda j: j.state == "running" and j.steps_done < j.steps)
                 dirty = True
                 continue
             self.chunks += 1
-            for job, _, _ in self.active:
-                if job.id in members:
-                    job.steps_done += n
+            for job in members:
+                job.steps_done += n
             dirty |= self._retire(lambda j: j.state == "running" and j.steps_done < j.steps)
         if batch is not None:
             self.backend.free_batch(batch)
         return self.stats(jobs)
+
+    def _member_errors(self, batch) -> dict:
+        if not hasattr(self.backend, "member_errors"):
+            return {}
+        try:
+            return self.backend.member_errors(batch)
+        except Exception:
+            return {}
 
     def stats(self, jobs: list) -> dict:
         done = [j for j in jobs if j.state == "done"]

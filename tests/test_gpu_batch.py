@@ -137,3 +137,32 @@ def test_batch_membership_rules(gpu_capi):
     b2.close()
     for s in (s1, s2, odd):
         s.close()
+
+
+def test_member_error_is_reported_per_member_and_isolated(gpu_capi):
+    """A member stepped far beyond the leapfrog stability bound grows until its
+    FP32 sums overflow and latches CE_ENONFINITE; ce_batch_status names it, and
+    the healthy member of the same batch is bit-identical to running alone."""
+    capi = gpu_capi
+    healthy_case = MIX[3]
+    f0, u0 = lattice_ics(1, 64, 20.0, 2, q=(1.2,), seed=5, amp=1e-2)
+    bad = capi.Simulation(dims=1, N=64, L=20.0, dt=1.0, nfields=2, q=(1.2,), expansion=True, precision="f32",
+                          kernel="generic", flags=capi.CE_FLAG_ALLOW_UNSTABLE_DT)
+    bad.set_fields(f0, u0)
+    good, _, _ = make_sim(capi, healthy_case, "f32", 31)
+    with capi.Batch([good, bad]) as b:
+        b.step(64)
+        with pytest.raises(capi.CeError) as ei:
+            b.synchronize()
+        assert ei.value.code == capi.CE_ENONFINITE
+        assert b.member_status() == [capi.CE_OK, capi.CE_ENONFINITE]
+    alone, _, _ = make_sim(capi, healthy_case, "f32", 31)
+    with capi.Batch([alone]) as b1:
+        b1.step(64)
+        assert b1.member_status() == [capi.CE_OK]
+    fa, va, sa = alone.get_fields(capi.CE_VEL_STAGGERED)
+    fg, vg, sg = good.get_fields(capi.CE_VEL_STAGGERED)
+    assert np.array_equal(fa, fg) and np.array_equal(va, vg)
+    assert (sa.a, sa.step) == (sg.a, sg.step)
+    for s in (bad, good, alone):
+        s.close()

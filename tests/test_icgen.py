@@ -42,3 +42,7 @@ def test_courant_dt():
     w = math.sqrt(12 / dx ** 2 + 3.0)
     assert courant_dt(3, 256, 20.0, 1.0, (1.2,)) == pytest.approx(0.9 / w)
     assert courant_dt(1, 8, 20.0, 1.0, (1.2,)) == 0.05
+    # masses at amp * phi0: a strongly coupled lattice takes a smaller step
+    w4 = math.sqrt(12.0 / (20.0 / 96) ** 2 + 72.9 * (4 * 1.98) ** 2)
+    assert courant_dt(3, 96, 20.0, 1.98, (72.9,), amp=4.0) == pytest.approx(0.9 / w4)
+    assert courant_dt(3, 96, 20.0, 1.98, (72.9,), amp=4.0) < 0.5 * courant_dt(3, 96, 20.0, 1.98, (72.9,))

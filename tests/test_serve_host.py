@@ -50,7 +50,11 @@ class FakeBackend:
         self.clock.t += n * self.step_cost
 
     def wait(self, batch):
-        pass
+        if any(h.get("status") for h in batch):
+            raise RuntimeError("a member reported non-finite sums")
+
+    def member_errors(self, batch):
+        return {k: h["status"] for k, h in enumerate(batch) if h.get("status")}
 
     def result(self, h):
         return {"steps": h["steps"]}
@@ -133,6 +137,27 @@ def test_injected_backend_failure_fails_the_chunk_and_the_server_carries_on():
     assert all(j.state == "failed" and "injected" in j.error for j in jobs[:3])
     assert jobs[3].state == "done" and jobs[3].result["steps"] == 50
     assert st["failed"] == 3 and st["done"] == 1
+
+
+def test_member_error_fails_only_that_job():
+    """A lattice that latches an error on the device (non-finite sums) fails
+    alone: the other members of its batch keep the chunk and finish."""
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    jobs = make_jobs(4, steps=100, gap=0.0)
+    orig_step = be.step
+
+    def step_and_poison(batch, n):
+        orig_step(batch, n)
+        if be.chunk == 2:
+            next(h for h in batch if h["id"] == 2)["status"] = -5
+    be.step = step_and_poison
+    st = Server(be, hbm_budget=1000, chunk_steps=20, clock=clock, sleep=clock.sleep).run(jobs)
+    assert jobs[2].state == "failed" and "member error -5" in jobs[2].error
+    for j in (jobs[0], jobs[1], jobs[3]):
+        assert j.state == "done" and j.result["steps"] == j.steps
+    assert st["failed"] == 1 and st["done"] == 3
+    assert sorted(be.freed) == [0, 1, 2, 3]
 
 
 def test_failed_admission_does_not_leak_budget():
