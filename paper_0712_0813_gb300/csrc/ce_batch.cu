@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -51,6 +52,7 @@ struct BMember {
   unsigned int* done;      // items of this lattice completed in the running launch
   double* partials;        // 2 doubles per item of this lattice
   int dims, N, p0, first_item, n_items, update_scalars;
+  int seg_log2;            // 3D: log2 of the lanes per row segment (5, 4 or 3: 1, 2 or 4 rows per warp)
   T inv_dx2, dt, q[3];
   double ddt, kappa2, inv_S, half_inv_dx2;
 };
@@ -107,10 +109,13 @@ __device__ __forceinline__ void lds16(const T* p, T (&o)[VX]) {
   }
 }
 
-// Shared-memory layout of one array (f or w of one field) in one ring stage:
-// 10 rows of one segment width (3D: the item's rows plus the two y-halo rows;
-// 2D/1D: row 0 holds the 8 warps' segments side by side), then 16 halo
-// elements (3D: left/right x-neighbours of each row; 2D/1D: of the span).
+// Shared-memory layout of one array (f or w of one field) in one ring stage.
+// 3D: the item's rows plus the two y-halo rows, each one segment wide (a
+// segment is LR = 32, 16 or 8 lanes x VX sites, so a warp holds 1, 2 or 4 rows
+// and an item 8, 16 or 32 rows), then two halo elements per row (left/right
+// x-neighbours).  2D/1D: row 0 holds the 8 warps' segments side by side and the
+// span's two halo elements follow the 10th row.  The widest segment (10 rows of
+// 32 VX + 16 halo elements) is the largest case and sizes the stage.
 template <typename T>
 struct Stage {
   static constexpr int VX = 16 / sizeof(T);
@@ -126,9 +131,11 @@ constexpr size_t batch_smem() {
 // One item, processed by the whole CTA: a cp.async ring of NST stages keeps up
 // to NST - 2 planes in flight while one is computed; one block barrier per plane
 // both publishes the landed plane and frees the slot read two planes earlier.
-// DIMS 3: warp w owns row y0 + w of a 32 x VX segment and sweeps z; DIMS 2: warp
-// w owns segment w of an 8-segment span of one row and sweeps y; DIMS 1: the
-// same span, one "plane".
+// DIMS 3: a row segment is LR = 2^seg_log2 lanes x VX sites; lane l of warp w
+// owns row r = w (32 / LR) + l / LR of the item, sites (l mod LR) VX .. + VX - 1
+// of the segment, and sweeps z (x-neighbour shuffles stay inside each LR-lane
+// group); DIMS 2: warp w owns segment w of an 8-segment span of one row and
+// sweeps y; DIMS 1: the same span, one "plane".
 template <typename T, int NF, int NST, int DIMS>
 __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int in, const BItem& it, T* smem,
                                          int warp, int lane, T& g2loc, T& vloc) {
@@ -137,22 +144,33 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
   const int64_t NN = (int64_t)N * N;
   // geometry of this warp
   int x0, nvl, nrows = 8;
-  bool wvalid;
+  // 3D segment geometry: lr lanes per row segment (32, 16 or 8), W sites wide
+  int lr = 32, sub = lane, r = warp, W = SEG, hbase = 10 * SEG;
+  bool wvalid, rvalid;
   if constexpr (DIMS == 3) {
-    nrows = min(8, N - it.y0);
-    wvalid = warp < nrows;
+    const int sl = m->seg_log2;
+    lr = 1 << sl;
+    sub = lane & (lr - 1);
+    r = (warp << (5 - sl)) + (lane >> sl);
+    W = lr * VX;
+    const int rows = 8 << (5 - sl);
+    hbase = (rows + 2) * W;
+    nrows = min(rows, N - it.y0);
+    wvalid = (warp << (5 - sl)) < nrows;
+    rvalid = r < nrows;
     x0 = it.x0;
-    nvl = min(32, (N - x0) / VX);
+    nvl = min(lr, (N - x0) / VX);
   } else {
     x0 = it.x0 + warp * SEG;
     wvalid = x0 < N;
+    rvalid = wvalid;
     nvl = wvalid ? min(32, (N - x0) / VX) : 0;
   }
-  const bool valid = wvalid && lane < nvl;
-  const int col = lane * VX;                     // column inside the warp's segment
+  const bool valid = rvalid && sub < nvl;
+  const int col = sub * VX;                      // column inside the lane's segment
   const int span_end = min(N, it.x0 + 8 * SEG);  // 2D/1D: end of the CTA's span
   const int last_warp = (span_end - it.x0 + SEG - 1) / SEG - 1;
-  const int y = it.y0 + warp;                    // 3D row
+  const int y = it.y0 + r;                       // 3D row
   const auto wrap = [&](int v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
   const int n = DIMS == 1 ? 1 : it.s1 - it.s0 + 2;
   const auto plane = [&](int j) { return DIMS == 1 ? 0 : wrap(it.s0 - 1 + j); };
@@ -161,6 +179,24 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
   T q[3] = {m->q[0], m->q[1], m->q[2]};
   const auto sbuf = [&](int slot, int i, int a) { return smem + ((size_t)(slot * NF + i) * 2 + a) * ARR; };
 
+  // Per-thread copies of one plane (3D; in-plane offsets, N^2 < 2^31 for any
+  // lattice that fits a GPU): the own 16 bytes, one 16-byte piece of the top
+  // (row 0) or bottom (row nrows - 1) y-halo row -- an item has at least two
+  // rows, so no thread has both -- and the x-halo elements at the row ends.
+  const int own_row = DIMS == 3 ? (r + 1) * W + col : warp * SEG + col;
+  int g_own = 0, g_hrow = 0, d_hrow = 0, g_xh = 0, g_xh2 = 0, d_xh = 0;
+  bool do_hrow = false, do_xh = false, do_xh2 = false;
+  if constexpr (DIMS == 3) {
+    g_own = y * N + x0 + col;
+    do_hrow = (r == 0 || r == nrows - 1) && sub < nvl;
+    g_hrow = (r == 0 ? wrap(it.y0 - 1) : wrap(it.y0 + nrows)) * N + x0 + col;
+    d_hrow = (r == 0 ? 0 : (nrows + 1) * W) + col;
+    do_xh = rvalid && (sub == 0 || sub == nvl - 1);
+    g_xh = y * N + (sub == 0 ? wrap(x0 - 1) : wrap(x0 + nvl * VX));
+    d_xh = hbase + 2 * r + (sub == 0 ? 0 : 1);
+    do_xh2 = rvalid && nvl == 1;   // a one-lane segment copies both ends
+    g_xh2 = y * N + wrap(x0 + nvl * VX);
+  }
   const auto issue = [&](int j) {
     const int slot = j % NST;
     const int64_t poff = DIMS == 3 ? (int64_t)plane(j) * NN : (DIMS == 2 ? (int64_t)plane(j) * N : 0);
@@ -171,13 +207,10 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
         const T* base = (a ? m->w[in][i] : m->f[in][i]) + poff;
         T* st = sbuf(slot, i, a);
         if constexpr (DIMS == 3) {
-          if (valid) cp16(st + (warp + 1) * SEG + col, base + (int64_t)y * N + x0 + col);
-          if (warp == 0 && lane < nvl) cp16(st + col, base + (int64_t)wrap(it.y0 - 1) * N + x0 + col);
-          if (warp == nrows - 1 && lane < nvl)
-            cp16(st + (nrows + 1) * SEG + col, base + (int64_t)wrap(it.y0 + nrows) * N + x0 + col);
-          if (wvalid && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG + 2 * warp, base + (int64_t)y * N + wrap(x0 - 1));
-          if (wvalid && lane == nvl - 1)
-            cp_small<sizeof(T)>(st + 10 * SEG + 2 * warp + 1, base + (int64_t)y * N + wrap(x0 + nvl * VX));
+          if (valid) cp16(st + own_row, base + g_own);
+          if (do_hrow) cp16(st + d_hrow, base + g_hrow);
+          if (do_xh) cp_small<sizeof(T)>(st + d_xh, base + g_xh);
+          if (do_xh2) cp_small<sizeof(T)>(st + d_xh + 1, base + g_xh2);
         } else {
           if (valid) cp16(st + warp * SEG + col, base + x0 + col);
           if (warp == 0 && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG, base + wrap(it.x0 - 1));
@@ -188,11 +221,11 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
     }
   };
   const auto gval = [&](T f, T w) { return fmaT(dd, fmaT(c, f, w), f); };
-  const int own_row = DIMS == 3 ? (warp + 1) * SEG + col : warp * SEG + col;
 
   // one plane's update at the own sites from registers (gp, gc, gn) and the
-  // staged current plane (y and x neighbours)
-  T gp[NF][VX], gc[NF][VX], vc[NF][VX];
+  // staged current plane (y and x neighbours, and the own sites' f, w again for
+  // v = w + c f: recomputing it is cheaper than holding it in registers)
+  T gp[NF][VX], gc[NF][VX];
   const auto update = [&](int j, const T (&gn)[NF][VX]) {
     const int slot = j % NST;
     const int zj = plane(j);
@@ -204,20 +237,20 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       T ym[VX], yp[VX];
       if constexpr (DIMS == 3) {
         T f[VX], w[VX];
-        lds16<T, VX>(cf + warp * SEG + col, f);
-        lds16<T, VX>(cw + warp * SEG + col, w);
+        lds16<T, VX>(cf + r * W + col, f);
+        lds16<T, VX>(cw + r * W + col, w);
 #pragma unroll
         for (int k = 0; k < VX; ++k) ym[k] = gval(f[k], w[k]);
-        lds16<T, VX>(cf + (warp + 2) * SEG + col, f);
-        lds16<T, VX>(cw + (warp + 2) * SEG + col, w);
+        lds16<T, VX>(cf + (r + 2) * W + col, f);
+        lds16<T, VX>(cw + (r + 2) * W + col, w);
 #pragma unroll
         for (int k = 0; k < VX; ++k) yp[k] = gval(f[k], w[k]);
       }
       // x neighbours: adjacent lanes; segment ends from the staged row or the halo
       T hl, hr;
       if constexpr (DIMS == 3) {
-        hl = gval(cf[10 * SEG + 2 * warp], cw[10 * SEG + 2 * warp]);
-        hr = gval(cf[10 * SEG + 2 * warp + 1], cw[10 * SEG + 2 * warp + 1]);
+        hl = gval(cf[hbase + 2 * r], cw[hbase + 2 * r]);
+        hr = gval(cf[hbase + 2 * r + 1], cw[hbase + 2 * r + 1]);
       } else {
         const int li = warp > 0 ? warp * SEG - 1 : 10 * SEG;
         const bool inner_r = x0 + nvl * VX < span_end;
@@ -225,10 +258,10 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
         hl = gval(cf[li], cw[li]);
         hr = gval(cf[ri], cw[ri]);
       }
-      T gl = __shfl_up_sync(0xffffffffu, gc[i][VX - 1], 1);
-      T gr = __shfl_down_sync(0xffffffffu, gc[i][0], 1);
-      if (lane == 0) gl = hl;
-      if (lane == nvl - 1) gr = hr;
+      T gl = __shfl_up_sync(0xffffffffu, gc[i][VX - 1], 1, lr);
+      T gr = __shfl_down_sync(0xffffffffu, gc[i][0], 1, lr);
+      if (sub == 0) gl = hl;
+      if (sub == nvl - 1) gr = hr;
 #pragma unroll
       for (int k = 0; k < VX; ++k) {
         const T g = gc[i][k];
@@ -250,6 +283,20 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
         if (valid) g2loc += d2;
       }
     }
+    T vc[NF][VX];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      T f[VX], w[VX];
+      if (valid) {
+        lds16<T, VX>(sbuf(slot, i, 0) + own_row, f);
+        lds16<T, VX>(sbuf(slot, i, 1) + own_row, w);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VX; ++k) f[k] = w[k] = T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < VX; ++k) vc[i][k] = fmaT(c, f[k], w[k]);
+    }
 #pragma unroll
     for (int k = 0; k < VX; ++k) {
       T gs[NF], dv[NF], vs;
@@ -261,7 +308,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       for (int i = 0; i < NF; ++i) lap[i][k] = fmaT(kk, lap[i][k] - dv[i], vc[i][k]);
     }
     if (valid) {
-      const int64_t here = DIMS == 3 ? (int64_t)zj * NN + (int64_t)y * N + x0 + col
+      const int64_t here = DIMS == 3 ? (int64_t)zj * NN + (y * N + x0 + col)
                                      : (DIMS == 2 ? (int64_t)zj * N + x0 + col : (int64_t)x0 + col);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
@@ -270,7 +317,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       }
     }
   };
-  const auto own_g = [&](int j, T (&g)[NF][VX], T (&v)[NF][VX], bool want_v) {
+  const auto own_g = [&](int j, T (&g)[NF][VX]) {
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
       T f[VX], w[VX];
@@ -282,11 +329,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
         for (int k = 0; k < VX; ++k) f[k] = w[k] = T(0);
       }
 #pragma unroll
-      for (int k = 0; k < VX; ++k) {
-        const T vv = fmaT(c, f[k], w[k]);
-        if (want_v) v[i][k] = vv;
-        g[i][k] = fmaT(dd, vv, f[k]);
-      }
+      for (int k = 0; k < VX; ++k) g[i][k] = fmaT(dd, fmaT(c, f[k], w[k]), f[k]);
     }
   };
 
@@ -301,7 +344,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
     __syncthreads();
     T none[NF][VX];
     if (wvalid) {
-      own_g(0, gc, vc, true);
+      own_g(0, gc);
       update(0, none);
     }
     return;
@@ -309,9 +352,8 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
     cp_wait<NST - 2>();   // planes 0 and 1 have landed
     __syncthreads();
     if (wvalid) {
-      T unused[NF][VX];
-      own_g(0, gp, unused, false);
-      own_g(1, gc, vc, true);
+      own_g(0, gp);
+      own_g(1, gc);
     }
     for (int j = 1; j <= n - 2; ++j) {
       cp_wait<NST - 3>();  // plane j + 1 has landed (own copies) ...
@@ -319,8 +361,8 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       if (j + NST - 1 < n) issue(j + NST - 1);
       cp_commit();
       if (wvalid) {
-        T gn[NF][VX], vn[NF][VX];
-        own_g(j + 1, gn, vn, true);
+        T gn[NF][VX];
+        own_g(j + 1, gn);
         update(j, gn);
 #pragma unroll
         for (int i = 0; i < NF; ++i)
@@ -328,7 +370,6 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
           for (int k = 0; k < VX; ++k) {
             gp[i][k] = gc[i][k];
             gc[i][k] = gn[i][k];
-            vc[i][k] = vn[i][k];
           }
       }
     }
@@ -336,7 +377,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
 }
 
 template <typename T, int NF, int NST>
-__global__ void __launch_bounds__(kThreads) k_step_batched(const BMember<T>* __restrict__ members,
+__global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(const BMember<T>* __restrict__ members,
                                                             const BItem* __restrict__ items, int n_items,
                                                             unsigned int* queue, int par) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
@@ -474,6 +515,36 @@ cudaError_t batch_prepare(int prec, int nf, int* per_sm) {
   return prec == CE_F32 ? prepare_t<float>(nf, per_sm) : prepare_t<double>(nf, per_sm);
 }
 
+// Lanes per 3D row segment, as log2: the segment width (32, 16 or 8 lanes x VX
+// sites) that pads a row of N sites least, the widest on a tie.  Depends on N
+// only, so a lattice's items do not depend on the rest of the batch.
+int seg_log2_for(int N, int VX) {
+  int best = 5;
+  int64_t best_pad = INT64_MAX;
+  for (int sl = 5; sl >= 3; --sl) {
+    const int64_t W = (int64_t)VX << sl;
+    const int64_t pad = (N + W - 1) / W * W;
+    if (pad < best_pad) {
+      best_pad = pad;
+      best = sl;
+    }
+  }
+  return best;
+}
+
+// Items build_tables cuts a lattice into (same loops, counted).
+int64_t item_count(int dims, int64_t N, int VX, int sweep_len) {
+  const int64_t L = std::max<int64_t>(1, std::min<int64_t>(sweep_len, N));
+  const int64_t span = ce::kWarps * 32 * VX;
+  if (dims == 3) {
+    const int sl = seg_log2_for((int)N, VX);
+    const int64_t W = (int64_t)VX << sl, rows = (int64_t)ce::kWarps << (5 - sl);
+    return ((N + W - 1) / W) * ((N + rows - 1) / rows) * ((N + L - 1) / L);
+  }
+  if (dims == 2) return ((N + span - 1) / span) * ((N + L - 1) / L);
+  return (N + span - 1) / span;
+}
+
 // Cut every member into items of about kWarps x 32 x VX x sweep_len sites.
 template <typename T>
 void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce::BItem>& items) {
@@ -492,10 +563,14 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
       per[k].push_back({ce::BItem{(int)k, x0, y0, s0, s1}, cost});
     };
     if (s->dims == 3) {
-      for (int x0 = 0; x0 < N; x0 += SEG)
-        for (int y0 = 0; y0 < N; y0 += ce::kWarps)
-          for (int z0 = 0; z0 < N; z0 += L)
-            add(x0, y0, z0, std::min(N, z0 + L), (int64_t)std::min(SEG, N - x0) * std::min(ce::kWarps, N - y0) * (std::min(N, z0 + L) - z0));
+      const int sl = seg_log2_for(N, VX);
+      const int W = VX << sl, rows = ce::kWarps << (5 - sl);
+      // x-neighbouring items next to each other in the queue, then y: items that
+      // share halo rows and halo sectors start together and read them from L2
+      for (int z0 = 0; z0 < N; z0 += L)
+        for (int y0 = 0; y0 < N; y0 += rows)
+          for (int x0 = 0; x0 < N; x0 += W)
+            add(x0, y0, z0, std::min(N, z0 + L), (int64_t)std::min(W, N - x0) * std::min(rows, N - y0) * (std::min(N, z0 + L) - z0));
     } else if (s->dims == 2) {
       for (int x0 = 0; x0 < N; x0 += ce::kWarps * SEG)
         for (int y0 = 0; y0 < N; y0 += L)
@@ -526,6 +601,7 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
     m.done = b->d_done + k;
     m.dims = s->dims;
     m.N = (int)s->N;
+    m.seg_log2 = s->dims == 3 ? seg_log2_for((int)s->N, VX) : 5;
     m.p0 = s->cur ^ b->par;
     m.first_item = (int)items.size();
     m.n_items = (int)per[k].size();
@@ -641,15 +717,10 @@ int ce::rows_create(ce_sim* s, ce_batch** out) {
     return bcuda(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "ce_create: row-kernel occupancy");
   }
   {
-    const int64_t N = s->N, seg = 32 * (16 / (int64_t)s->esize);
+    const int VX = 16 / s->esize;
     for (int L = 128; L >= 4; L /= 2) {
       b->sweep_len = L;
-      const int64_t Ls = std::min<int64_t>(L, N);
-      int64_t items;
-      if (s->dims == 3) items = ((N + seg - 1) / seg) * ((N + 7) / 8) * ((N + Ls - 1) / Ls);
-      else if (s->dims == 2) items = ((N + 8 * seg - 1) / (8 * seg)) * ((N + Ls - 1) / Ls);
-      else items = (N + 8 * seg - 1) / (8 * seg);
-      if (items >= 2LL * per_sm * sms) break;
+      if (item_count(s->dims, s->N, VX, L) >= 2LL * per_sm * sms) break;
     }
   }
   const int cur = s->cur;

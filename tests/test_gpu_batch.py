@@ -2,8 +2,10 @@
 
 * Each member of a mixed 1D/2D/3D batch matches the FP64 oracle (<= 1e-11
   relative max error after 30 steps), including ragged row segments (N not a
-  multiple of the 32-lane segment), partial 8-row groups and lattices with
-  and without expansion in the same launch.
+  multiple of the segment), every 3D segment width (32, 16 and 8 lanes per
+  row), partial row groups, 1D lattices swept over several spans with a
+  partial last span, and lattices with and without expansion in the same
+  launch.
 * "The same alone and in the mix": a lattice advanced in a batch of one and
   inside the mix is bit-identical (its items and their summation order do not
   depend on the other members), in FP32 and FP64.
@@ -23,6 +25,7 @@ MIX = [
     (2, 100, 2, (1.2,), True, 0.05),
     (2, 256, 2, (5.0,), True, 0.02),
     (1, 4096, 2, (1.2,), True, 0.004),
+    (1, 2600, 2, (3.0,), True, 0.004),  # full spans swept + a partial last span
     (1, 36, 2, (40.0,), False, 0.02),
 ]
 
