@@ -178,6 +178,16 @@ int ce_energy(ce_sim* sim, ce_energy_t* out);
  * Synchronises. */
 int ce_get_fields(ce_sim* sim, double* f, double* v, int mode, ce_scalars_t* sc);
 
+/* The staggered state at n chosen sites, without downloading the lattice (for
+ * probing lattices of many GB; no counterpart in the paper).  sites: host
+ * array of n linear site indices x + N y + N^2 z in [0, N^dims).  f, v: host
+ * float64 arrays of nf * n, field-major (f[i * n + k] is field i at sites[k]);
+ * v = f'(t+dt/2) formed exactly as ce_get_fields(CE_VEL_STAGGERED) forms it.
+ * *sc (required) receives the scalars.  Synchronises.
+ * Errors: CE_EINVAL (NULL argument, n < 0, a site out of range), CE_ESTATE (no
+ * fields set), a latched device error, CE_ECUDA. */
+int ce_sample_fields(ce_sim* sim, const int64_t* sites, int64_t n, double* f, double* v, ce_scalars_t* sc);
+
 /* Release the handle and its device memory.  NULL-safe. */
 void ce_free(ce_sim* sim);
 

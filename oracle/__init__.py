@@ -15,6 +15,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                          constraint drift O(dt^2), time reversibility
   orc_energy/orc_means_variances pinned: numpy definitions
   spectrum (numpy FFT + binning) pinned: Parseval, plane-wave and constant fields
+  local.step_at (one step at chosen sites, numpy; ``oracle/local.py``) pinned:
+                         bit-identical to orc_step on whole small lattices
   start-up conventions (a(0)=1, u-velocity, kappa default), the IC recipe and the
   Courant rule are conventions the paper leaves open: parity unpinned there.
 """

@@ -62,7 +62,7 @@ EXPORTS = ("ce_create", "ce_set_fields", "ce_step", "ce_synchronize", "ce_means_
            "ce_energy", "ce_get_fields", "ce_free", "ce_last_error", "ce_device_bytes",
            "ce_kernel_in_use", "ce_sweep_plan", "ce_replan", "ce_version", "ce_moments_noalloc",
            "ce_spectrum", "ce_save", "ce_load",
-           "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_status", "ce_batch_info",
+           "ce_sample_fields", "ce_batch_create", "ce_batch_step", "ce_batch_synchronize", "ce_batch_status", "ce_batch_info",
            "ce_batch_free")
 
 
@@ -104,6 +104,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "ce_moments_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp, vp, vp]),
         "ce_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, P(vp)]),
         "ce_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "ce_sample_fields": (ctypes.c_int, [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_double),
+                                            P(ctypes.c_double), P(ce_scalars_t)]),
         "ce_batch_synchronize": (ctypes.c_int, [vp]),
         "ce_batch_status": (ctypes.c_int, [vp, P(ctypes.c_int), ctypes.c_int]),
         "ce_batch_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
@@ -222,6 +224,19 @@ def ce_get_fields(sim, nfields: int, sites: int, mode: int = CE_VEL_SYNC, out=No
         f, v = out
     sc = ce_scalars_t()
     _check(load().ce_get_fields(sim, _dptr(f), _dptr(v), int(mode), ctypes.byref(sc)))
+    return f, v, sc
+
+
+def ce_sample_fields(sim, nfields: int, sites):
+    """Staggered state at the given linear site indices: (f, v, scalars), f and v
+    float64 arrays of shape (nfields, len(sites))."""
+    idx = np.ascontiguousarray(sites, dtype=np.int64).reshape(-1)
+    n = idx.size
+    f = np.empty((nfields, n))
+    v = np.empty((nfields, n))
+    sc = ce_scalars_t()
+    _check(load().ce_sample_fields(sim, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n,
+                                   _dptr(f), _dptr(v), ctypes.byref(sc)))
     return f, v, sc
 
 
@@ -383,6 +398,9 @@ class Simulation:
 
     def get_fields(self, mode=CE_VEL_SYNC):
         return ce_get_fields(self.handle, self.nfields, self.sites, mode)
+
+    def sample_fields(self, sites):
+        return ce_sample_fields(self.handle, self.nfields, sites)
 
     @property
     def kernel(self):

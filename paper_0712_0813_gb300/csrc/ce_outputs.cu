@@ -1,7 +1,8 @@
 // ce_outputs.cu -- outputs beyond the means and energies: the binned power
-// spectrum of a field (cuFFT transform + binning kernel) and the grid-image
-// file (a complete state that ce_load restores exactly; arXiv:0712.0813 Sec. II
-// describes grid images that let a run be resumed later).
+// spectrum of a field (cuFFT transform + binning kernel), the grid-image file
+// (a complete state that ce_load restores exactly; arXiv:0712.0813 Sec. II
+// describes grid images that let a run be resumed later), and the state at
+// chosen sites (a gather, for probing lattices too large to download).
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -13,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "ce_device.cuh"
 #include "ce_internal.h"
 #include "clusterlat.h"
 
@@ -26,6 +28,28 @@ int ofail(int code, const std::string& msg) {
 int ocuda(cudaError_t e, const char* what) {
   ce::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
   return CE_ECUDA;
+}
+
+// f(t) and f'(t + dt/2) = w + c f at m chosen sites, for every field; the
+// velocity is rounded in T exactly as the step kernels and ce_get_fields form it.
+template <typename T>
+struct SamplePtrs {
+  const T* f[4];
+  const T* w[4];
+};
+
+template <typename T>
+__global__ void k_sample(SamplePtrs<T> p, int nf, const ce::DevScalars* sc, const int64_t* __restrict__ sites,
+                         int64_t m, double* __restrict__ out_f, double* __restrict__ out_v) {
+  const T c = (T)sc->c;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = sites[k];
+    for (int i = 0; i < nf; ++i) {
+      const T fv = p.f[i][x], wv = p.w[i][x];
+      out_f[(int64_t)i * m + k] = (double)fv;
+      out_v[(int64_t)i * m + k] = (double)ce::fmaT(c, fv, wv);
+    }
+  }
 }
 
 constexpr int kBinThreads = 256;
@@ -226,6 +250,72 @@ int ce_spectrum(ce_sim* s, int field, int nbins, double* k, double* power, doubl
     power[b] = host[b];
     count[b] = host[nbins + b];
   }
+  return CE_OK;
+}
+
+int ce_sample_fields(ce_sim* s, const int64_t* sites, int64_t n, double* f, double* v, ce_scalars_t* sc) {
+  ce::set_last_error("");
+  if (!s) return ofail(CE_EINVAL, "ce_sample_fields: sim is NULL");
+  if (n < 0 || (n > 0 && (!sites || !f || !v)) || !sc) return ofail(CE_EINVAL, "ce_sample_fields: bad arguments");
+  if (!s->have_state) return ofail(CE_ESTATE, "ce_sample_fields: no fields set");
+  for (int64_t k = 0; k < n; ++k)
+    if (sites[k] < 0 || sites[k] >= s->S) return ofail(CE_EINVAL, "ce_sample_fields: site index out of range");
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e == cudaSuccess && s->batch) e = ce::batch_wait(s->batch);
+  if (e != cudaSuccess) return ocuda(e, "ce_sample_fields");
+  // the staging buffer (chunk x nf doubles) holds, per pass, m site indices and
+  // the m x nf values of f and of v
+  const int64_t cap = s->chunk * s->nf * 8;
+  const int64_t mmax = std::max<int64_t>(1, cap / (8 + 16 * (int64_t)s->nf));
+  unsigned char* stage = reinterpret_cast<unsigned char*>(s->staging);
+  const void* slot = &s->aux->slot[s->cur];
+  for (int64_t k0 = 0; k0 < n; k0 += mmax) {
+    const int64_t m = std::min<int64_t>(mmax, n - k0);
+    int64_t* d_sites = reinterpret_cast<int64_t*>(stage);
+    double* d_f = reinterpret_cast<double*>(stage + m * 8);
+    double* d_v = d_f + m * s->nf;
+    e = cudaMemcpyAsync(d_sites, sites + k0, (size_t)m * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return ocuda(e, "ce_sample_fields: site upload");
+    const int blocks = (int)std::min<int64_t>((m + 255) / 256, 152 * 4);
+    if (s->prec == CE_F32) {
+      SamplePtrs<float> p{};
+      for (int i = 0; i < s->nf; ++i) {
+        p.f[i] = static_cast<const float*>(s->f[s->cur][i]);
+        p.w[i] = static_cast<const float*>(s->w[s->cur][i]);
+      }
+      k_sample<float><<<blocks, 256, 0, s->stream>>>(p, s->nf, static_cast<const ce::DevScalars*>(slot), d_sites, m,
+                                                     d_f, d_v);
+    } else {
+      SamplePtrs<double> p{};
+      for (int i = 0; i < s->nf; ++i) {
+        p.f[i] = static_cast<const double*>(s->f[s->cur][i]);
+        p.w[i] = static_cast<const double*>(s->w[s->cur][i]);
+      }
+      k_sample<double><<<blocks, 256, 0, s->stream>>>(p, s->nf, static_cast<const ce::DevScalars*>(slot), d_sites, m,
+                                                      d_f, d_v);
+    }
+    e = cudaGetLastError();
+    for (int i = 0; i < s->nf && e == cudaSuccess; ++i) {
+      e = cudaMemcpyAsync(f + (int64_t)i * n + k0, d_f + (int64_t)i * m, (size_t)m * 8, cudaMemcpyDeviceToHost,
+                          s->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v + (int64_t)i * n + k0, d_v + (int64_t)i * m, (size_t)m * 8, cudaMemcpyDeviceToHost,
+                            s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return ocuda(e, "ce_sample_fields: gather");
+  }
+  ce::DevAux host{};
+  e = cudaMemcpyAsync(&host, s->aux, sizeof(host), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return ocuda(e, "ce_sample_fields: scalars");
+  if (host.status != CE_OK) return ofail(host.status, "ce_sample_fields: the device reported an error");
+  const ce::DevScalars& d = host.slot[s->cur];
+  sc->a = s->cfg.expansion ? d.a : 1.0;
+  sc->ap_half = s->cfg.expansion ? d.ap : 0.0;
+  sc->app = s->cfg.expansion ? d.app : 0.0;
+  sc->t = s->t;
+  sc->step = s->step;
   return CE_OK;
 }
 

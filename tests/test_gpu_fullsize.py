@@ -1,0 +1,173 @@
+"""Parity at the full benchmark sizes, on sampled sites.
+
+The lattices of the benchmark workloads are too large to download and step on
+the host (1024^3 x 2 fields is 17 GB per FP64 array, and the oracle needs about
+a hundred seconds per step there), so one GPU step is checked site by site:
+
+* the staggered state (f(t), v(t+dt/2)) is sampled on the GPU
+  (`ce_sample_fields`) at a few thousand sites -- random ones plus every
+  combination of tile edges, lattice edges and z-chunk boundaries of the launch
+  plan -- and at their nearest neighbours;
+* the GPU takes one step, and the new state is sampled at the sites;
+* the oracle's per-site restatement of one step (`oracle/local.py`, pinned
+  equal to `orc_step` on whole lattices) computes the new state from the first
+  sample.  The step's global sums G and V enter only the scale factor; the
+  oracle takes them from `ce_energy` (the separate diagnostic kernel's FP64 sums
+  of the stored fields), so the scale factor the fused step kernel computed from
+  its own FP32 partial sums is checked against them too.
+
+Workloads and launch plans are the ones the benchmark times: 3D 256^3, 2
+fields, dt = 0.02 (plan 8 rows / 4 stages / 4 z-chunks); 3D 512^3, 4 fields,
+q = (0.8, 5, 40) (plan 8 / 5 / 8); 3D 1024^3, 2 fields (plan 16 / 4 / 8); all
+FP32 storage with expansion; and the 96-lattice mixed batch (FP32, batched
+kernel, the item length the bench's autotuner picks).  Tolerances: f and v
+within an error bound of one FP32 step derived from the arithmetic
+(`check_one_step`; on the finest lattices the Laplacian's 1/dx^2 weights make
+the FP32 rounding of g the dominant term), a(t) to 1e-12, and a', a'' to 1e-5
+of the source term Q (FP32 partial sums of the fused kernel against FP64
+sums).
+"""
+import gc
+
+import numpy as np
+import pytest
+
+from paper_0712_0813_gb300.icgen import courant_dt, lattice_ics
+
+pytestmark = pytest.mark.gpu
+
+KAPPA2 = 8.0 * np.pi / 3.0 * 0.342 ** 2
+
+
+def relmax(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def plan_sites(N, tx, ty, zchunks, n_random=3000, seed=11):
+    """Random sites plus every combination of tile, lattice and z-chunk edges."""
+    xs = sorted({0, 1, tx - 1, tx, tx + 1, N // 2, N - tx, N - 2, N - 1})
+    ys = sorted({0, 1, ty - 1, ty, N // 2, N - ty, N - 1})
+    zb = {0, 1, N - 2, N - 1}
+    for j in range(1, zchunks):
+        z = j * N // zchunks
+        zb |= {z - 1, z, z + 1}
+    xx, yy, zz = np.meshgrid(np.array(xs), np.array(ys), np.array(sorted(zb)), indexing="ij")
+    edges = (xx + N * yy + N * N * zz).reshape(-1)
+    rng = np.random.default_rng(seed)
+    rand = rng.integers(0, N ** 3, size=n_random)
+    return np.unique(np.concatenate([edges, rand]).astype(np.int64))
+
+
+EPS32 = 2.0 ** -24   # unit roundoff of FP32 storage
+
+
+def check_one_step(orc, local, p, before, after, sites, stencil, G, V):
+    """before/after: (f, v, scalars) sampled at stencil / sites.
+
+    Error bound of one FP32 step against FP64 arithmetic on the same stored
+    inputs (the oracle starts from the sampled FP32 values, so only the step's
+    own roundings count): f' = g = f + dt v is one rounding of |f| + dt |v|;
+    v' = v + dt (lap g - dV/df(g) + s g) carries the rounding of every g it
+    reads multiplied by the Laplacian's weights (sum 4 d / dx^2), of dV/df and
+    of the sum, each a few units of EPS32.  Eight units per term leave room
+    for the FMA/non-FMA differences and the final conversions."""
+    fb, vb, scb = before
+    fa, va, sca = after
+    ref = local.step_at(p, sites, stencil, fb, vb, scb.a, scb.ap_half, G, V)
+    dxinv2 = (p.N / p.L) ** 2
+    s = ref.app / ref.a
+    q = list(p.q) + [0.0] * 3
+    gm = [float(np.abs(ref.f[i]).max()) for i in range(p.nf)]
+    # |dV/df_i| bounds: phi^3 + phi sum q chi^2, and q_i phi^2 chi_i
+    dvm = [gm[0] ** 3 + gm[0] * sum(q[j - 1] * gm[j] ** 2 for j in range(1, p.nf))]
+    dvm += [q[i - 1] * gm[0] ** 2 * gm[i] for i in range(1, p.nf)]
+    for i in range(p.nf):
+        vmax = float(np.abs(vb[i]).max())
+        tol_f = 4.0 * EPS32 * (float(np.abs(fb[i]).max()) + p.dt * vmax)
+        tol_v = 8.0 * EPS32 * (vmax + p.dt * ((4 * p.dims + 2) * dxinv2 * gm[i] + dvm[i] + abs(s) * gm[i]))
+        assert np.abs(fa[i] - ref.f[i]).max() <= tol_f, (i, np.abs(fa[i] - ref.f[i]).max(), tol_f)
+        assert np.abs(va[i] - ref.v[i]).max() <= tol_v, (i, np.abs(va[i] - ref.v[i]).max(), tol_v)
+    assert abs(sca.a - ref.a) <= 1e-12 * ref.a
+    Q = p.kappa2 * (2.0 * G + 3.0 * V) / ref.a
+    scale = abs(Q) + ref.ap ** 2 / ref.a
+    assert abs(sca.app - ref.app) <= 1e-5 * scale
+    assert abs(sca.ap_half - ref.ap) <= 1e-5 * p.dt * scale + 1e-12 * abs(ref.ap)
+
+
+SINGLE = [
+    # name, N, nf, q, dt (None: Courant rule), plan (rows, stages, zchunks)
+    ("256cube", 256, 2, (1.2,), 0.02, (8, 4, 4)),
+    ("512cube_4field", 512, 4, (0.8, 5.0, 40.0), None, (8, 5, 8)),
+    ("1024cube", 1024, 2, (1.2,), None, (16, 4, 8)),
+]
+
+
+@pytest.mark.parametrize("name,N,nf,q,dt,plan", SINGLE, ids=[c[0] for c in SINGLE])
+def test_full_size_sampled_step(gpu_capi, orc, name, N, nf, q, dt, plan):
+    import torch
+    from oracle import local
+    capi = gpu_capi
+    L = 20.0
+    if dt is None:
+        dt = courant_dt(3, N, L, 1.0, q)
+    f0, u0 = lattice_ics(3, N, L, nf, q=q, seed=1, backend="torch" if N >= 512 else "numpy")
+    torch.cuda.empty_cache()
+    rows, stages, zchunks = plan
+    with capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision="f32",
+                         kernel="sweep", tile_rows=rows, stages=stages, zchunks=zchunks) as sim:
+        assert sim.sweep_plan == plan
+        sim.set_fields(f0, u0)
+        del f0, u0
+        gc.collect()
+        sim.step(3)
+        sites = plan_sites(N, 128, rows, zchunks)
+        stencil = local.stencil_sites(3, N, sites)
+        before = sim.sample_fields(stencil)
+        sim.step(1)
+        after = sim.sample_fields(sites)
+        en = sim.energy()
+    p = orc.Params(dims=3, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
+    check_one_step(orc, local, p, before, after, sites, stencil, float(np.sum(en["G"])), en["V"])
+    assert after[2].step == 4
+
+
+def test_mixed_batch_sampled_step(gpu_capi, orc):
+    """The 96-lattice mix of the batched benchmark leg, one batched launch per
+    step at the autotuned item length: every member checked on sampled sites."""
+    import torch
+    from oracle import local
+    from paper_0712_0813_gb300 import autotune, workloads
+    capi = gpu_capi
+    specs = workloads.mixed_batch_specs()
+    sims = []
+    for sp in specs:
+        s = capi.Simulation(**workloads.sim_kwargs(sp, "f32"), kernel="generic")
+        s.set_fields(*workloads.make_ics(sp))
+        sims.append(s)
+    stream = torch.cuda.Stream()
+    tune = autotune.autotune_batch(sims, stream=stream, steps=4, warmup=1)
+    rng = np.random.default_rng(17)
+    picks, befores = [], []
+    with capi.Batch(sims, sweep_len=tune["sweep_len"], stream=stream.cuda_stream) as b:
+        b.step(2)
+        b.synchronize()
+        for sp, s in zip(specs, sims):
+            S = workloads.sites(sp)
+            n = min(S, 400)
+            edge = np.array([0, 1, sp["N"] - 1, S - 1, S // 2], dtype=np.int64)
+            sites = np.unique(np.concatenate([edge, rng.integers(0, S, size=n)]))
+            stencil = local.stencil_sites(sp["dims"], sp["N"], sites)
+            picks.append((sites, stencil))
+            befores.append(s.sample_fields(stencil))
+        b.step(1)
+        b.synchronize()
+    for sp, s, (sites, stencil), before in zip(specs, sims, picks, befores):
+        after = s.sample_fields(sites)
+        en = s.energy()
+        p = orc.Params(dims=sp["dims"], N=sp["N"], L=sp["L"], dt=sp["dt"], nf=sp["nf"], q=sp["q"],
+                       expansion=sp["expansion"])
+        check_one_step(orc, local, p, before, after, sites, stencil, float(np.sum(en["G"])), en["V"])
+        s.close()

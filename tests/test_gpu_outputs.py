@@ -55,3 +55,33 @@ def test_grid_image_round_trip_continues_bit_identically(gpu_capi, tmp_path):
         with pytest.raises(capi.CeError) as ei:
             c.load(path)
         assert ei.value.code == capi.CE_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_sample_fields_equals_full_download(gpu_capi, precision):
+    """ce_sample_fields returns exactly the values ce_get_fields(CE_VEL_STAGGERED)
+    returns at the same sites, in chunks when the sites outnumber the staging
+    buffer; bad indices and a handle without fields are errors."""
+    capi = gpu_capi
+    N, nf = 24, 3
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=(0.8, 5.0), seed=4, amp=1e-2)
+    with capi.Simulation(dims=3, N=N, L=20.0, dt=0.02, nfields=nf, q=(0.8, 5.0), expansion=True,
+                         precision=precision) as sim:
+        with pytest.raises(capi.CeError) as ei:
+            sim.sample_fields([0])
+        assert ei.value.code == capi.CE_ESTATE
+        sim.set_fields(f0, u0)
+        sim.step(7)
+        f, v, sc = sim.get_fields(capi.CE_VEL_STAGGERED)
+        rng = np.random.default_rng(2)
+        sites = rng.integers(0, N ** 3, size=5 * N ** 3)          # repeats, several staging passes
+        fs, vs, ss = sim.sample_fields(sites)
+        assert np.array_equal(fs, f.reshape(nf, -1)[:, sites])
+        assert np.array_equal(vs, v.reshape(nf, -1)[:, sites])
+        assert (ss.a, ss.ap_half, ss.app, ss.step) == (sc.a, sc.ap_half, sc.app, sc.step)
+        empty = sim.sample_fields(np.zeros(0, dtype=np.int64))
+        assert empty[0].shape == (nf, 0)
+        for bad in ([-1], [N ** 3]):
+            with pytest.raises(capi.CeError) as ei:
+                sim.sample_fields(bad)
+            assert ei.value.code == capi.CE_EINVAL

@@ -363,3 +363,46 @@ def test_spectrum_plane_wave_and_constant(orc):
     assert np.delete(power * count, 5).max() < 1e-18 * power[5] * count[5]
     k, power, count = orc.spectrum(p, np.full(S, 1.5), 12)
     assert power[0] == pytest.approx((1.5 * S) ** 2) and count[0] == 1
+
+
+LOCAL_CASES = [
+    # dims, N, nf, q, expansion, dt
+    (3, 6, 2, (1.2,), True, 0.05),
+    (3, 5, 4, (0.8, 5.0, 40.0), True, 0.03),
+    (2, 9, 3, (0.8, 5.0), False, 0.05),
+    (1, 11, 1, (), True, 0.02),
+    (3, 3, 2, (1.2,), True, 0.05),          # every neighbour wraps
+]
+
+
+@pytest.mark.parametrize("dims,N,nf,q,expansion,dt", LOCAL_CASES)
+def test_local_step_equals_orc_step(orc, dims, N, nf, q, expansion, dt):
+    """The per-site restatement of one step (oracle/local.py), evaluated at
+    every site from the whole state and fed the G, V of the drifted fields,
+    reproduces orc_step exactly; evaluated at a subset of sites from the state
+    at those sites' stencil only, it gives the same numbers there."""
+    from oracle import local
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    L = 20.0 if N > 5 else 3.0
+    p = orc.Params(dims=dims, N=N, L=L, dt=dt, nf=nf, q=q if q else (0.0,), expansion=expansion)
+    f0, u0 = lattice_ics(dims, N, L, nf, q=q if q else (1.2,), seed=21, amp=3e-2)
+    st = orc.init(p, f0, u0)
+    S = p.S
+    fb, vb = st.f.copy().reshape(nf, S), st.v.copy().reshape(nf, S)
+    a, ap = st.scale.a, st.scale.ap
+    drifted = (fb + p.dt * vb).reshape(-1)
+    G = orc.gradient_mean(p, drifted)[0]
+    V = orc.potential_mean(p, drifted)
+    orc.step(st, 1)
+    everywhere = np.arange(S)
+    res = local.step_at(p, everywhere, everywhere, fb, vb, a, ap, G, V)
+    assert np.array_equal(res.f, st.f.reshape(nf, S))
+    assert np.array_equal(res.v, st.v.reshape(nf, S))
+    assert (res.a, res.ap, res.app) == (st.scale.a, st.scale.ap, st.scale.app)
+    rng = np.random.default_rng(5)
+    some = np.sort(rng.choice(S, size=max(1, S // 3), replace=False))
+    sten = local.stencil_sites(dims, N, some)
+    part = local.step_at(p, some, sten, fb[:, sten], vb[:, sten], a, ap, G, V)
+    assert np.array_equal(part.f, res.f[:, some]) and np.array_equal(part.v, res.v[:, some])
+    with pytest.raises(ValueError):
+        local.step_at(p, some, some, fb[:, some], vb[:, some], a, ap, G, V)   # neighbours missing
