@@ -56,7 +56,7 @@ __host__ __device__ constexpr size_t halo_bytes(int ty) { return ((size_t)ty * 1
 template <typename T>
 constexpr size_t smem_bytes(int nf, int ty, int stages) {
   return (size_t)stages * nf * 2 * ((ty + 2) * (32 * (16 / sizeof(T))) * sizeof(T) + 2 * halo_bytes(ty)) +
-         2 * stages * sizeof(uint64_t) + 128;
+         3 * stages * sizeof(uint64_t) + 128;
 }
 
 // Resident CTAs per SM the kernel is compiled for (register budget): as many
@@ -124,6 +124,22 @@ __device__ __forceinline__ void lds16(const T* p, T (&o)[VX]) {
   }
 }
 
+// VX consecutive values of one row: one 16-byte shared-memory store.
+template <typename T, int VX>
+__device__ __forceinline__ void sts16(T* p, const T (&o)[VX]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  }
+}
+
+// Orders this thread's shared-memory writes before later TMA (async-proxy)
+// writes to the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // 16-byte streaming store to HBM (the next step reads it back from HBM anyway).
 template <typename T, int VX>
 __device__ __forceinline__ void stg16(T* p, const T (&o)[VX]) {
@@ -151,6 +167,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
   T* stage = reinterpret_cast<T*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)NST * NF * 2 * ARR * sizeof(T));
   uint64_t* empty = full + NST;
+  uint64_t* gready = empty + NST;   // all consumer warps wrote their g rows into a slot
   __shared__ int s_abort;
   __shared__ int s_min_waited;
 
@@ -179,6 +196,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], TY);
+      mbar_init(&gready[s], TY);
     }
     s_abort = 0;
     s_min_waited = nplanes;
@@ -243,9 +261,38 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
     T g2loc = T(0), vloc = T(0);
     T gp[NF][VX], gc[NF][VX], vc[NF][VX];
     int waited = 0;
+    // A slot goes back to the producer once nobody reads it; the consumers also
+    // wrote g rows into it, which the next TMA fill overwrites.
     auto release = [&](int pidx) {
+      fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[pidx % NST]);
+    };
+    // Each warp replaces the f of its own staged row by g = f + dt (w + c f)
+    // (warps 0 and TY-1 also convert the y-halo rows), so the rows above and
+    // below read their y-neighbours' g instead of recomputing it from f and w;
+    // the g values are the same numbers either way.  gready[slot] completes
+    // when all TY warps have written the slot (every plane position, written
+    // or not, so its phases stay in step with the ring).
+    auto put_g = [&](int slot, const T (&g)[NF][VX]) {
+#pragma unroll
+      for (int i = 0; i < NF; ++i) sts16<T, VX>(sbuf(slot, i, 0) + (r + 1) * TX + col, g[i]);
+      if (r == 0 || r == TY - 1) {
+        const int hr = (r == 0) ? 0 : TY + 1;
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {
+          T f[VX], w[VX], h[VX];
+          lds16<T, VX>(sbuf(slot, i, 0) + hr * TX + col, f);
+          lds16<T, VX>(sbuf(slot, i, 1) + hr * TX + col, w);
+#pragma unroll
+          for (int j = 0; j < VX; ++j) h[j] = fmaT(dd, fmaT(c, f[j], w[j]), f[j]);
+          sts16<T, VX>(sbuf(slot, i, 0) + hr * TX + col, h);
+        }
+      }
+    };
+    auto publish = [&](int pidx) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&gready[pidx % NST]);
     };
     bool ok = __all_sync(0xffffffffu, wait_bar(&full[0], 0u));
     if (ok) {
@@ -258,6 +305,7 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
 #pragma unroll
         for (int j = 0; j < VX; ++j) gp[i][j] = fmaT(dd, fmaT(c, f[j], w[j]), f[j]);
       }
+      publish(0);   // plane 0 is only a z-neighbour: no g rows needed
       release(0);
       ok = __all_sync(0xffffffffu, wait_bar(&full[1 % NST], (uint32_t)(1 / NST) & 1u));
     }
@@ -274,6 +322,8 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
           gc[i][j] = fmaT(dd, vc[i][j], f[j]);
         }
       }
+      put_g(1 % NST, gc);
+      publish(1);
     }
     for (int pc = 1; pc <= nplanes - 2 && ok; ++pc) {
       const int z = plane_z(pc);  // the plane computed now
@@ -287,31 +337,30 @@ __global__ void __launch_bounds__(32 * (TY + 1), (min_blocks<T, NF, TY, NST>()))
       // gp / gc / gn: g at the previous, current and next plane of the sweep
       T gn[NF][VX], vn[NF][VX], lap[NF][VX];
 #pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        {  // next plane, own sites
-          T f[VX], w[VX];
-          lds16<T, VX>(sbuf(sc_nxt, i, 0) + (r + 1) * TX + col, f);
-          lds16<T, VX>(sbuf(sc_nxt, i, 1) + (r + 1) * TX + col, w);
+      for (int i = 0; i < NF; ++i) {  // next plane, own sites
+        T f[VX], w[VX];
+        lds16<T, VX>(sbuf(sc_nxt, i, 0) + (r + 1) * TX + col, f);
+        lds16<T, VX>(sbuf(sc_nxt, i, 1) + (r + 1) * TX + col, w);
 #pragma unroll
-          for (int j = 0; j < VX; ++j) {
-            vn[i][j] = fmaT(c, f[j], w[j]);
-            gn[i][j] = fmaT(dd, vn[i][j], f[j]);
-          }
+        for (int j = 0; j < VX; ++j) {
+          vn[i][j] = fmaT(c, f[j], w[j]);
+          gn[i][j] = fmaT(dd, vn[i][j], f[j]);
         }
+      }
+      if (pn <= nplanes - 2) put_g(sc_nxt, gn);   // the last plane is only a z-neighbour
+      publish(pn);
+      // the current plane's g rows, written by all warps one plane ago
+      if (!__all_sync(0xffffffffu, wait_bar(&gready[sc_cur], (uint32_t)(pc / NST) & 1u))) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
         const T* cf = sbuf(sc_cur, i, 0);
         const T* cw = sbuf(sc_cur, i, 1);
         T ym[VX], yp[VX];
-        {  // y neighbours in the current plane
-          T f[VX], w[VX];
-          lds16<T, VX>(cf + r * TX + col, f);
-          lds16<T, VX>(cw + r * TX + col, w);
-#pragma unroll
-          for (int j = 0; j < VX; ++j) ym[j] = fmaT(dd, fmaT(c, f[j], w[j]), f[j]);
-          lds16<T, VX>(cf + (r + 2) * TX + col, f);
-          lds16<T, VX>(cw + (r + 2) * TX + col, w);
-#pragma unroll
-          for (int j = 0; j < VX; ++j) yp[j] = fmaT(dd, fmaT(c, f[j], w[j]), f[j]);
-        }
+        lds16<T, VX>(cf + r * TX + col, ym);          // g of the row below (y - 1)
+        lds16<T, VX>(cf + (r + 2) * TX + col, yp);    // g of the row above (y + 1)
         // x neighbours: adjacent lanes; the row ends read the TMA'd halo columns
         const int hoff = (lane == 0) ? MAIN + r * H + (H - 1) : MAIN + HALO + r * H;
         const T hf = cf[hoff], hw = cw[hoff];
