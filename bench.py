@@ -52,7 +52,7 @@ WORKLOADS = {
 }
 WORKLOAD = WORKLOADS["256cube"]
 METRIC = "Gsite-updates/s"
-STEP_SOURCES = {"k_step_sweep": ("ce_sweep3d.cuh", "ce_sweep3d_f32.cu", "ce_device.cuh", "ce_internal.h"),
+STEP_SOURCES = {"k_step_sweep": ("ce_sweep3d.cuh", "ce_sweep3d_f32.cu", "ce_tma.cuh", "ce_device.cuh", "ce_internal.h"),
                 "k_step_generic": ("ce_generic.cu", "ce_device.cuh", "ce_internal.h")}
 
 

@@ -25,6 +25,8 @@
 // and advances its a, a', a'' -- nobody waits for anybody.  The last CTA to
 // leave resets the queue for the next launch.  One launch advances every
 // lattice by one step; step loops are CUDA graphs of 32 launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,12 +37,19 @@
 
 #include "ce_device.cuh"
 #include "ce_internal.h"
+#include "ce_tma.cuh"
 
 namespace ce {
 namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
+// Tensor-map box shapes of a 3D member, per (buffer parity, field, f or w):
+// row boxes one segment wide and rows + 2, rows + 1, 1, nlast + 1 and nlast
+// rows high (nlast: rows of the lattice's last row group), then x-halo column
+// boxes 16 bytes wide and rows or nlast rows high.
+constexpr int kMapTypes = 7;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: bound of every device-side wait
 constexpr int kBatchGraphSteps = 32;
 
 template <typename T>
@@ -53,6 +62,7 @@ struct BMember {
   double* partials;        // 2 doubles per item of this lattice
   int dims, N, p0, first_item, n_items, update_scalars;
   int seg_log2;            // 3D: log2 of the lanes per row segment (5, 4 or 3: 1, 2 or 4 rows per warp)
+  const CUtensorMap* tmaps;  // 3D: tensor maps of f, w (see kMapTypes), device memory; else null
   T inv_dx2, dt, q[3];
   double ddt, kappa2, inv_S, half_inv_dx2;
 };
@@ -112,33 +122,42 @@ __device__ __forceinline__ void lds16(const T* p, T (&o)[VX]) {
 // Shared-memory layout of one array (f or w of one field) in one ring stage.
 // 3D: the item's rows plus the two y-halo rows, each one segment wide (a
 // segment is LR = 32, 16 or 8 lanes x VX sites, so a warp holds 1, 2 or 4 rows
-// and an item 8, 16 or 32 rows), then two halo elements per row (left/right
-// x-neighbours).  2D/1D: row 0 holds the 8 warps' segments side by side and the
-// span's two halo elements follow the 10th row.  The widest segment (10 rows of
-// 32 VX + 16 halo elements) is the largest case and sizes the stage.
+// and an item rows = 8, 16 or 32 rows: (rows + 2) W sites, which is 8 SEG + 2 W),
+// then the left and the right x-halo columns, 16 bytes (VX sites) per row each,
+// as TMA delivers them.  2D/1D: row 0 holds the 8 warps' segments side by side
+// and the span's two halo elements follow the 10th row.  The largest 3D case
+// (10 rows of 32 VX plus 2 x 8 x VX halo sites, or 34 rows of 8 VX plus
+// 2 x 32 x VX) sizes the stage; ARR x sizeof(T) is a multiple of 128 bytes, so
+// every TMA destination stays 128-byte aligned.
 template <typename T>
 struct Stage {
   static constexpr int VX = 16 / sizeof(T);
   static constexpr int SEG = 32 * VX;
-  static constexpr int ARR = 10 * SEG + 16;
+  static constexpr int ARR = 10 * SEG + 16 * VX;
+  static_assert((ARR * sizeof(T)) % 128 == 0, "stage arrays must keep TMA destinations 128-byte aligned");
 };
 
 template <typename T, int NF, int NST>
 constexpr size_t batch_smem() {
-  return (size_t)NST * NF * 2 * Stage<T>::ARR * sizeof(T);
+  return (size_t)NST * NF * 2 * Stage<T>::ARR * sizeof(T) + 128;   // + alignment slack
 }
 
-// One item, processed by the whole CTA: a cp.async ring of NST stages keeps up
-// to NST - 2 planes in flight while one is computed; one block barrier per plane
+// One item, processed by the whole CTA: a ring of NST stages keeps up to
+// NST - 2 planes in flight while one is computed; one block barrier per plane
 // both publishes the landed plane and frees the slot read two planes earlier.
+// 3D planes arrive by TMA (thread 0 issues one or two row boxes and two x-halo
+// column boxes per array from the member's tensor maps; full[slot] completes
+// when the bytes have landed, every thread waits on it with a bounded wait and
+// keeps the slot's phase in bit slot of ph); 2D/1D planes by per-thread
+// cp.async.  Returns false when a wait ran out (the caller stops).
 // DIMS 3: a row segment is LR = 2^seg_log2 lanes x VX sites; lane l of warp w
 // owns row r = w (32 / LR) + l / LR of the item, sites (l mod LR) VX .. + VX - 1
 // of the segment, and sweeps z (x-neighbour shuffles stay inside each LR-lane
 // group); DIMS 2: warp w owns segment w of an 8-segment span of one row and
 // sweeps y; DIMS 1: the same span, one "plane".
 template <typename T, int NF, int NST, int DIMS>
-__device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int in, const BItem& it, T* smem,
-                                         int warp, int lane, T& g2loc, T& vloc) {
+__device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int in, const BItem& it, T* smem,
+                                         uint64_t* full, uint32_t& ph, int warp, int lane, T& g2loc, T& vloc) {
   constexpr int VX = Stage<T>::VX, SEG = Stage<T>::SEG, ARR = Stage<T>::ARR;
   const int N = m->N;
   const int64_t NN = (int64_t)N * N;
@@ -179,46 +198,75 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
   T q[3] = {m->q[0], m->q[1], m->q[2]};
   const auto sbuf = [&](int slot, int i, int a) { return smem + ((size_t)(slot * NF + i) * 2 + a) * ARR; };
 
-  // Per-thread copies of one plane (3D; in-plane offsets, N^2 < 2^31 for any
-  // lattice that fits a GPU): the own 16 bytes, one 16-byte piece of the top
-  // (row 0) or bottom (row nrows - 1) y-halo row -- an item has at least two
-  // rows, so no thread has both -- and the x-halo elements at the row ends.
   const int own_row = DIMS == 3 ? (r + 1) * W + col : warp * SEG + col;
-  int g_own = 0, g_hrow = 0, d_hrow = 0, g_xh = 0, g_xh2 = 0, d_xh = 0;
-  bool do_hrow = false, do_xh = false, do_xh2 = false;
-  if constexpr (DIMS == 3) {
-    g_own = y * N + x0 + col;
-    do_hrow = (r == 0 || r == nrows - 1) && sub < nvl;
-    g_hrow = (r == 0 ? wrap(it.y0 - 1) : wrap(it.y0 + nrows)) * N + x0 + col;
-    d_hrow = (r == 0 ? 0 : (nrows + 1) * W) + col;
-    do_xh = rvalid && (sub == 0 || sub == nvl - 1);
-    g_xh = y * N + (sub == 0 ? wrap(x0 - 1) : wrap(x0 + nvl * VX));
-    d_xh = hbase + 2 * r + (sub == 0 ? 0 : 1);
-    do_xh2 = rvalid && nvl == 1;   // a one-lane segment copies both ends
-    g_xh2 = y * N + wrap(x0 + nvl * VX);
-  }
+  // 3D: the staged rows 0 .. nrows + 1 hold lattice rows y0 - 1 .. y0 + nrows
+  // (mod N): one box where they do not wrap, else a box per contiguous run;
+  // box heights are those of the member's tensor maps (kMapTypes).  The x-halo
+  // columns are the 16-byte chunks holding sites x0 - 1 and x0 + len (mod N).
+  const int rows3 = DIMS == 3 ? 8 << (5 - m->seg_log2) : 8;
+  const uint32_t plane_bytes =
+      (uint32_t)(NF * 2 * ((nrows + 2) * W * (int)sizeof(T) + 2 * nrows * 16));
   const auto issue = [&](int j) {
     const int slot = j % NST;
-    const int64_t poff = DIMS == 3 ? (int64_t)plane(j) * NN : (DIMS == 2 ? (int64_t)plane(j) * N : 0);
+    if constexpr (DIMS == 3) {
+      if (threadIdx.x != 0) return;
+      const int zz = plane(j);
+      const int y0 = it.y0;
+      const int len = min(W, N - x0);
+      const int xl = x0 >= VX ? x0 - VX : N - VX, xr = x0 + len < N ? x0 + len : 0;
+      const int hts = nrows == rows3 ? 5 : 6;        // x-halo map: rows or nlast rows high
+      mbar_expect_tx(&full[slot], plane_bytes);
 #pragma unroll
-    for (int i = 0; i < NF; ++i) {
+      for (int i = 0; i < NF; ++i) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const T* base = (a ? m->w[in][i] : m->f[in][i]) + poff;
-        T* st = sbuf(slot, i, a);
-        if constexpr (DIMS == 3) {
-          if (valid) cp16(st + own_row, base + g_own);
-          if (do_hrow) cp16(st + d_hrow, base + g_hrow);
-          if (do_xh) cp_small<sizeof(T)>(st + d_xh, base + g_xh);
-          if (do_xh2) cp_small<sizeof(T)>(st + d_xh + 1, base + g_xh2);
-        } else {
-          if (valid) cp16(st + warp * SEG + col, base + x0 + col);
-          if (warp == 0 && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG, base + wrap(it.x0 - 1));
-          if (warp == last_warp && lane == nvl - 1)
-            cp_small<sizeof(T)>(st + 10 * SEG + 1, base + (span_end == N ? 0 : span_end));
+        for (int a = 0; a < 2; ++a) {
+          T* st = sbuf(slot, i, a);
+          const CUtensorMap* mp = m->tmaps + ((in * NF + i) * 2 + a) * kMapTypes;
+          if (y0 >= 1 && y0 + nrows <= N - 1) {          // no wrap: rows y0-1 .. y0+rows
+            tma_load_3d(st, mp + 0, x0, y0 - 1, zz, &full[slot]);
+          } else if (y0 == 0 && nrows < N) {            // first group: row N-1, then 0 .. rows
+            tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
+            tma_load_3d(st + W, mp + 1, x0, 0, zz, &full[slot]);
+          } else if (y0 == 0) {                         // one group holds every row
+            tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
+            tma_load_3d(st + W, mp + 4, x0, 0, zz, &full[slot]);
+            tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
+          } else {                                      // last group: rows y0-1 .. N-1, then row 0
+            tma_load_3d(st, mp + 3, x0, y0 - 1, zz, &full[slot]);
+            tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
+          }
+          tma_load_3d(st + hbase, mp + hts, xl, y0, zz, &full[slot]);
+          tma_load_3d(st + hbase + rows3 * VX, mp + hts, xr, y0, zz, &full[slot]);
+        }
+      }
+      return;
+    } else {
+      const int64_t poff = DIMS == 2 ? (int64_t)plane(j) * N : 0;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const T* base = (a ? m->w[in][i] : m->f[in][i]) + poff;
+          T* st = sbuf(slot, i, a);
+          {
+            if (valid) cp16(st + warp * SEG + col, base + x0 + col);
+            if (warp == 0 && lane == 0) cp_small<sizeof(T)>(st + 10 * SEG, base + wrap(it.x0 - 1));
+            if (warp == last_warp && lane == nvl - 1)
+              cp_small<sizeof(T)>(st + 10 * SEG + 1, base + (span_end == N ? 0 : span_end));
+          }
         }
       }
     }
+  };
+  // 3D: bounded wait for plane j's bytes (~2 s of clock); keeps the slot phase.
+  const auto wait_plane = [&](int j) -> bool {
+    const int slot = j % NST;
+    const uint32_t parity = (ph >> slot) & 1u;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&full[slot], parity))
+      if (clock64() - t0 > kWaitCycles) return false;
+    ph ^= 1u << slot;
+    return true;
   };
   const auto gval = [&](T f, T w) { return fmaT(dd, fmaT(c, f, w), f); };
 
@@ -249,8 +297,9 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       // x neighbours: adjacent lanes; segment ends from the staged row or the halo
       T hl, hr;
       if constexpr (DIMS == 3) {
-        hl = gval(cf[hbase + 2 * r], cw[hbase + 2 * r]);
-        hr = gval(cf[hbase + 2 * r + 1], cw[hbase + 2 * r + 1]);
+        const int li = hbase + r * VX + (VX - 1), ri = hbase + rows3 * VX + r * VX;
+        hl = gval(cf[li], cw[li]);
+        hr = gval(cf[ri], cw[ri]);
       } else {
         const int li = warp > 0 ? warp * SEG - 1 : 10 * SEG;
         const bool inner_r = x0 + nvl * VX < span_end;
@@ -337,8 +386,22 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
 #pragma unroll
   for (int j = 0; j < NST; ++j) {
     if (j < n) issue(j);
-    cp_commit();
+    if constexpr (DIMS != 3) cp_commit();
   }
+  int issued = min(n, NST), waited = 0;
+  // 3D: every thread waits for plane j's bytes, then the block barrier; when a
+  // wait ran out, all threads stop and thread 0 waits (bounded) for the copies
+  // still in flight, so no TMA write lands after the CTA's shared memory is gone.
+  const auto landed = [&](int j) -> bool {
+    const bool ok = wait_plane(j);
+    if (ok) waited = j + 1;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0)
+        for (int pl = waited; pl < issued; ++pl) wait_plane(pl);
+      return false;
+    }
+    return true;
+  };
   if constexpr (DIMS == 1) {
     cp_wait<0>();
     __syncthreads();
@@ -347,19 +410,30 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       own_g(0, gc);
       update(0, none);
     }
-    return;
+    return true;
   } else {
-    cp_wait<NST - 2>();   // planes 0 and 1 have landed
-    __syncthreads();
+    if constexpr (DIMS == 3) {
+      if (!landed(0) || !landed(1)) return false;
+    } else {
+      cp_wait<NST - 2>();   // planes 0 and 1 have landed
+      __syncthreads();
+    }
     if (wvalid) {
       own_g(0, gp);
       own_g(1, gc);
     }
     for (int j = 1; j <= n - 2; ++j) {
-      cp_wait<NST - 3>();  // plane j + 1 has landed (own copies) ...
-      __syncthreads();     // ... for every thread, and plane j - 1's slot is free
-      if (j + NST - 1 < n) issue(j + NST - 1);
-      cp_commit();
+      if constexpr (DIMS == 3) {
+        if (!landed(j + 1)) return false;   // plane j + 1 is in, plane j - 1's slot is free
+      } else {
+        cp_wait<NST - 3>();  // plane j + 1 has landed (own copies) ...
+        __syncthreads();     // ... for every thread, and plane j - 1's slot is free
+      }
+      if (j + NST - 1 < n) {
+        issue(j + NST - 1);
+        issued = j + NST;
+      }
+      if constexpr (DIMS != 3) cp_commit();
       if (wvalid) {
         T gn[NF][VX];
         own_g(j + 1, gn);
@@ -374,6 +448,7 @@ __device__ __forceinline__ void run_item(const BMember<T>* __restrict__ m, int i
       }
     }
   }
+  return true;
 }
 
 template <typename T, int NF, int NST>
@@ -381,9 +456,18 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
                                                             const BItem* __restrict__ items, int n_items,
                                                             unsigned int* queue, int par) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
-  T* smem = reinterpret_cast<T*>(smem_dyn);
+  // 128-byte aligned for the TMA destinations (an offset of the shared array,
+  // so the pointer stays in the shared space)
+  T* smem = reinterpret_cast<T*>(smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u));
   __shared__ int s_item;
+  __shared__ __align__(8) uint64_t s_full[NST];   // TMA completion of each ring slot (3D items)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(&s_full[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t ph = 0;   // phase bit of each s_full slot; the same in every thread
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(&queue[0], 1u);
     __syncthreads();
@@ -393,9 +477,14 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
     const BMember<T>* m = members + it.member;
     const int in = m->p0 ^ par;
     T g2loc = T(0), vloc = T(0);
-    if (m->dims == 3) run_item<T, NF, NST, 3>(m, in, it, smem, warp, lane, g2loc, vloc);
-    else if (m->dims == 2) run_item<T, NF, NST, 2>(m, in, it, smem, warp, lane, g2loc, vloc);
-    else run_item<T, NF, NST, 1>(m, in, it, smem, warp, lane, g2loc, vloc);
+    bool ok;
+    if (m->dims == 3) ok = run_item<T, NF, NST, 3>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
+    else if (m->dims == 2) ok = run_item<T, NF, NST, 2>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
+    else ok = run_item<T, NF, NST, 1>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
+    if (!ok) {   // a bounded wait ran out: report it on the lattice and stop this CTA
+      if (threadIdx.x == 0) atomicCAS(m->status, CE_OK, CE_ETIMEOUT);
+      break;
+    }
     if (m->update_scalars) {
       double g2 = (double)g2loc, pot = (double)vloc;
       block_sum2(g2, pot);
@@ -445,6 +534,7 @@ struct ce_batch {
   unsigned int* d_queue = nullptr;   // [0] head, [1] exit count
   unsigned int* d_done = nullptr;    // per member
   double* d_partials = nullptr;      // 2 per item
+  void* d_maps = nullptr;            // tensor maps of the 3D members
   int n_items = 0, blocks = 0, par = 0, sweep_len = 32;
   int ctas_per_sm = 0;               // cap on resident CTAs per SM (0: as many as fit)
   int64_t sites = 0;
@@ -617,6 +707,69 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
   }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor maps of every 3D member's f and w (both buffer sets): the x/y/z box
+// shapes of kMapTypes for the member's segment width and row-group height.
+template <typename T>
+int encode_maps(ce_batch* b, std::vector<ce::BMember<T>>& mem) {
+  constexpr int VX = 16 / sizeof(T);
+  size_t n3 = 0;
+  for (const ce_sim* s : b->members) n3 += s->dims == 3;
+  if (n3 == 0) return CE_OK;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = map_encoder();
+  if (!enc) return bfail(CE_ECUDA, "ce_batch_create: no tensor-map encoder in the driver");
+  const size_t per = (size_t)2 * b->nf * 2 * ce::kMapTypes;
+  std::vector<CUtensorMap> maps(n3 * per);
+  size_t at = 0;
+  std::vector<size_t> first(b->members.size(), 0);
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    const ce_sim* s = b->members[k];
+    if (s->dims != 3) continue;
+    first[k] = at;
+    const int64_t N = s->N;
+    const int sl = seg_log2_for((int)N, VX);
+    const cuuint32_t W = (cuuint32_t)(VX << sl), rows = (cuuint32_t)(ce::kWarps << (5 - sl));
+    const cuuint32_t groups = (cuuint32_t)((N + rows - 1) / rows);
+    const cuuint32_t nlast = (cuuint32_t)(N - (int64_t)rows * (groups - 1));
+    const cuuint32_t bw[ce::kMapTypes] = {W, W, W, W, W, (cuuint32_t)VX, (cuuint32_t)VX};
+    const cuuint32_t bh[ce::kMapTypes] = {rows + 2, rows + 1, 1, nlast + 1, nlast, rows, nlast};
+    const cuuint64_t gdim[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N};
+    const cuuint64_t gstride[2] = {(cuuint64_t)N * sizeof(T), (cuuint64_t)N * N * sizeof(T)};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i < b->nf; ++i)
+        for (int a = 0; a < 2; ++a)
+          for (int t = 0; t < ce::kMapTypes; ++t) {
+            const cuuint32_t box[3] = {bw[t], bh[t], 1};
+            CUresult r = enc(&maps[at++], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                             3, a == 0 ? s->f[p][i] : s->w[p][i], gdim, gstride, box, estride,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return bfail(CE_ECUDA, "ce_batch_create: tensor-map encoding failed");
+          }
+  }
+  cudaError_t e = cudaMalloc(&b->d_maps, maps.size() * sizeof(CUtensorMap));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return bcuda(e, "ce_batch_create: tensor maps");
+  const CUtensorMap* dm = static_cast<const CUtensorMap*>(b->d_maps);
+  for (size_t k = 0; k < b->members.size(); ++k)
+    mem[k].tmaps = b->members[k]->dims == 3 ? dm + first[k] : nullptr;
+  return CE_OK;
+}
+
 template <typename T>
 int upload_tables(ce_batch* b) {
   std::vector<ce::BMember<T>> mem;
@@ -627,6 +780,7 @@ int upload_tables(ce_batch* b) {
   cudaError_t e = cudaMalloc(&b->d_partials, sizeof(double) * 2 * std::max(1, b->n_items));
   if (e != cudaSuccess) return bcuda(e, "ce_batch_create: partials");
   for (auto& m : mem) m.partials = b->d_partials + 2 * (int64_t)m.first_item;
+  if (int rc = encode_maps<T>(b, mem)) return rc;
   e = cudaMalloc(&b->d_members, sizeof(ce::BMember<T>) * mem.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(ce::BItem) * std::max<size_t>(1, items.size()));
   if (e == cudaSuccess)
@@ -644,6 +798,7 @@ void release(ce_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_queue) cudaFree(b->d_queue);
   if (b->d_partials) cudaFree(b->d_partials);
+  if (b->d_maps) cudaFree(b->d_maps);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
