@@ -382,7 +382,10 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
     }
   };
 
-  // prologue: fill the ring
+  // prologue: fill the ring (3D: the fence orders a previous 2D/1D item's
+  // cp.async writes into the same slots before these TMA writes)
+  if constexpr (DIMS == 3)
+    if (threadIdx.x == 0) fence_proxy_async_smem();
 #pragma unroll
   for (int j = 0; j < NST; ++j) {
     if (j < n) issue(j);

@@ -93,12 +93,6 @@ __device__ __forceinline__ void sts16(T* p, const T (&o)[VX]) {
   }
 }
 
-// Orders this thread's shared-memory writes before later TMA (async-proxy)
-// writes to the same bytes.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // 16-byte streaming store to HBM (the next step reads it back from HBM anyway).
 template <typename T, int VX>
 __device__ __forceinline__ void stg16(T* p, const T (&o)[VX]) {
