@@ -337,7 +337,8 @@ def run_reference(args):
     value = (N ** 3) * args.steps / el / 1e9
     sample = f"each step = one oracle step of a {N}^3 sub-lattice of the same model (bounded sample of the 256^3 workload)"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "device": "host CPU (the oracle; no GPU work)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w["name"], "sample_N": N, "precision": "f64",
