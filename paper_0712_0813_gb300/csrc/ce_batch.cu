@@ -145,8 +145,8 @@ constexpr size_t batch_smem() {
 // One item, processed by the whole CTA: a ring of NST stages keeps up to
 // NST - 2 planes in flight while one is computed; one block barrier per plane
 // both publishes the landed plane and frees the slot read two planes earlier.
-// 3D planes arrive by TMA (thread 0 issues one or two row boxes and two x-halo
-// column boxes per array from the member's tensor maps; full[slot] completes
+// 3D planes arrive by TMA (one lane per array issues one or two row boxes and two
+// x-halo column boxes from the member's tensor maps; full[slot] completes
 // when the bytes have landed, every thread waits on it with a bounded wait and
 // keeps the slot's phase in bit slot of ph); 2D/1D planes by per-thread
 // cp.async.  Returns false when a wait ran out (the caller stops).
@@ -209,36 +209,34 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
   const auto issue = [&](int j) {
     const int slot = j % NST;
     if constexpr (DIMS == 3) {
-      if (threadIdx.x != 0) return;
+      // thread 0 posts the plane's bytes; lane 0 of warp w issues the boxes of
+      // field w / 2, array (f, w) w % 2 (a complete_tx may run ahead of the
+      // expect_tx: the phase cannot end before thread 0's arrival)
+      if (threadIdx.x == 0) mbar_expect_tx(&full[slot], plane_bytes);
+      if (lane != 0 || warp >= 2 * NF) return;
+      const int i = warp >> 1, a = warp & 1;
       const int zz = plane(j);
       const int y0 = it.y0;
       const int len = min(W, N - x0);
       const int xl = x0 >= VX ? x0 - VX : N - VX, xr = x0 + len < N ? x0 + len : 0;
       const int hts = nrows == rows3 ? 5 : 6;        // x-halo map: rows or nlast rows high
-      mbar_expect_tx(&full[slot], plane_bytes);
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          T* st = sbuf(slot, i, a);
-          const CUtensorMap* mp = m->tmaps + ((in * NF + i) * 2 + a) * kMapTypes;
-          if (y0 >= 1 && y0 + nrows <= N - 1) {          // no wrap: rows y0-1 .. y0+rows
-            tma_load_3d(st, mp + 0, x0, y0 - 1, zz, &full[slot]);
-          } else if (y0 == 0 && nrows < N) {            // first group: row N-1, then 0 .. rows
-            tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
-            tma_load_3d(st + W, mp + 1, x0, 0, zz, &full[slot]);
-          } else if (y0 == 0) {                         // one group holds every row
-            tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
-            tma_load_3d(st + W, mp + 4, x0, 0, zz, &full[slot]);
-            tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
-          } else {                                      // last group: rows y0-1 .. N-1, then row 0
-            tma_load_3d(st, mp + 3, x0, y0 - 1, zz, &full[slot]);
-            tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
-          }
-          tma_load_3d(st + hbase, mp + hts, xl, y0, zz, &full[slot]);
-          tma_load_3d(st + hbase + rows3 * VX, mp + hts, xr, y0, zz, &full[slot]);
-        }
+      T* st = sbuf(slot, i, a);
+      const CUtensorMap* mp = m->tmaps + ((in * NF + i) * 2 + a) * kMapTypes;
+      if (y0 >= 1 && y0 + nrows <= N - 1) {          // no wrap: rows y0-1 .. y0+rows
+        tma_load_3d(st, mp + 0, x0, y0 - 1, zz, &full[slot]);
+      } else if (y0 == 0 && nrows < N) {            // first group: row N-1, then 0 .. rows
+        tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
+        tma_load_3d(st + W, mp + 1, x0, 0, zz, &full[slot]);
+      } else if (y0 == 0) {                         // one group holds every row
+        tma_load_3d(st, mp + 2, x0, N - 1, zz, &full[slot]);
+        tma_load_3d(st + W, mp + 4, x0, 0, zz, &full[slot]);
+        tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
+      } else {                                      // last group: rows y0-1 .. N-1, then row 0
+        tma_load_3d(st, mp + 3, x0, y0 - 1, zz, &full[slot]);
+        tma_load_3d(st + (nrows + 1) * W, mp + 2, x0, 0, zz, &full[slot]);
       }
+      tma_load_3d(st + hbase, mp + hts, xl, y0, zz, &full[slot]);
+      tma_load_3d(st + hbase + rows3 * VX, mp + hts, xr, y0, zz, &full[slot]);
       return;
     } else {
       const int64_t poff = DIMS == 2 ? (int64_t)plane(j) * N : 0;
@@ -382,10 +380,13 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
     }
   };
 
-  // prologue: fill the ring (3D: the fence orders a previous 2D/1D item's
-  // cp.async writes into the same slots before these TMA writes)
-  if constexpr (DIMS == 3)
-    if (threadIdx.x == 0) fence_proxy_async_smem();
+  // prologue: fill the ring (3D: every thread's fence, then the barrier, order
+  // a previous 2D/1D item's cp.async writes into the same slots before these
+  // TMA writes)
+  if constexpr (DIMS == 3) {
+    fence_proxy_async_smem();
+    __syncthreads();
+  }
 #pragma unroll
   for (int j = 0; j < NST; ++j) {
     if (j < n) issue(j);
