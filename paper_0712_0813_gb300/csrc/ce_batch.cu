@@ -7,17 +7,20 @@
 // (g(x+e_d) - g(x))^2 and V(g) that advance each lattice's own scale factor.
 //
 // Work decomposition.  Every lattice of the batch is cut into work items of
-// about the same size: a CTA of 8 warps takes one item; each warp owns one row
-// segment of 32 lanes x VX consecutive x-sites (VX = 16 B / sizeof(T)) and
-// sweeps it along the slowest axis (z in 3D, y in 2D; 1D items have no sweep).
-// Each plane of the item (f and w of every field: the 8 rows, in 3D also the
-// two y-halo rows, and the single x-halo elements at the segment ends) is
-// copied into a shared-memory ring with cp.async, so loads in flight hold no
-// registers; one block barrier per plane publishes the landed plane and frees
+// about the same size, and a CTA of 8 warps takes one item, swept along the
+// lattice's slowest axis (z in 3D, y in 2D; 1D items have no sweep).  3D: rows
+// of one segment of 32, 16 or 8 lanes x VX sites (VX = 16 B / sizeof(T); the
+// width that pads a row of N sites least), so a warp holds 1, 2 or 4 rows;
+// 2D/1D: each warp owns one 32-lane segment of a row.  Each plane of the item
+// (f and w of every field, in 3D with the two y-halo rows and the x-halo
+// columns) is staged in a shared-memory ring: 3D planes by TMA tensor copies
+// from per-lattice tensor maps (one lane per field and array issues the boxes,
+// an mbarrier per slot signals their arrival), 2D/1D planes by per-thread
+// cp.async.  One block barrier per plane publishes the landed plane and frees
 // the slot read two planes earlier.  Sweep-axis neighbours stay in registers,
-// x-neighbours come from the adjacent lane by shuffle and from the staged halo
-// elements, y-neighbours from the staged rows.  Segments may be partial (N not a
-// multiple of 32 VX): lanes past the row end idle.
+// x-neighbours come from the adjacent lane by shuffle and from the staged halo,
+// y-neighbours from the staged rows.  Segments may be partial (N not a multiple
+// of the segment): lanes past the row end idle.
 //
 // The grid is persistent: a fixed number of resident CTAs pull items from one
 // queue (an atomic counter), largest items first.  The CTA that completes the
