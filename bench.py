@@ -459,7 +459,7 @@ def main():
     alg_bytes = 4 * esize * w["nf"] * S          # read f, w; write f, w per field and site
     launch_s = secs / args.steps                  # one step kernel per step
     achieved = alg_bytes / launch_s / 1e9
-    kname = "k_step_sweep" if kernel == "sweep" else "k_step_generic"
+    kname = {"sweep": "k_step_sweep", "rows": "k_step_batched"}.get(kernel, "k_step_generic")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": ncu_traffic(kname, args.precision),
                 "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}

@@ -24,8 +24,9 @@
 //
 // The grid is persistent: a fixed number of resident CTAs pull items from one
 // queue (an atomic counter), largest items first.  The CTA that completes the
-// last item of a lattice combines that lattice's item partials in item order
-// and advances its a, a', a'' -- nobody waits for anybody.  The last CTA to
+// last item of a lattice combines that lattice's item partials (all its
+// threads, in an order fixed by the lattice's item count) and advances its a,
+// a', a'' -- nobody waits for anybody.  The last CTA to
 // leave resets the queue for the next launch.  One launch advances every
 // lattice by one step; step loops are CUDA graphs of 32 launches.
 #include <cuda.h>
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
   // 128-byte aligned for the TMA destinations (an offset of the shared array,
   // so the pointer stays in the shared space)
   T* smem = reinterpret_cast<T*>(smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u));
-  __shared__ int s_item;
+  __shared__ int s_item, s_last;
   __shared__ __align__(8) uint64_t s_full[NST];   // TMA completion of each ring slot (3D items)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -500,14 +501,21 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
         m->partials[2 * k] = g2;
         m->partials[2 * k + 1] = pot;
         __threadfence();
-        if (atomicAdd(m->done, 1u) == (unsigned int)(m->n_items - 1)) {
-          // last item of this lattice: combine in item order, advance a
-          __threadfence();
-          double G = 0.0, V = 0.0;
-          for (int j = 0; j < m->n_items; ++j) {
-            G += __ldcg(m->partials + 2 * j);
-            V += __ldcg(m->partials + 2 * j + 1);
-          }
+        s_last = atomicAdd(m->done, 1u) == (unsigned int)(m->n_items - 1);
+      }
+      __syncthreads();
+      if (s_last) {
+        // last item of this lattice: the whole CTA combines the item partials
+        // (thread t takes items t, t + blockDim, ..., then a fixed tree, so the
+        // order depends on the lattice's item count alone) and advances a
+        __threadfence();
+        double G = 0.0, V = 0.0;
+        for (int j = threadIdx.x; j < m->n_items; j += blockDim.x) {
+          G += __ldcg(m->partials + 2 * j);
+          V += __ldcg(m->partials + 2 * j + 1);
+        }
+        block_sum2(G, V);
+        if (threadIdx.x == 0) {
           DevScalars out;
           scale_factor_update(m->slot[in], out, G * m->half_inv_dx2 * m->inv_S, V * m->inv_S, m->ddt,
                               m->kappa2, m->status);
@@ -844,6 +852,66 @@ void advance_members(ce_batch* b, int64_t steps) {
 
 cudaError_t ce::batch_wait(ce_batch* b) { return b ? cudaStreamSynchronize(b->stream) : cudaSuccess; }
 
+namespace {
+
+// Predicted duration, in plane-times, of one launch on a lattice alone cut into
+// items of L planes along the sweep axis (plus two halo planes and a start-up
+// cost of about two planes each), taken from the queue in build order by
+// `slots` resident CTAs.  The active CTAs share HBM equally and one CTA streams
+// at most 1.25x its share under full load: a processor-sharing model whose two
+// constants were chosen on timings of single 2D and 3D lattices (a lattice of
+// few columns needs short items to keep the CTAs busy, a large one long items
+// to amortise the halo planes, and a fraction of a wave costs a whole item).
+double rows_predicted_time(int dims, int64_t N, int VX, int L, int slots) {
+  const int64_t Lc = std::max<int64_t>(1, std::min<int64_t>(L, N));
+  const int64_t nz = (N + Lc - 1) / Lc, last = N - (nz - 1) * Lc;
+  const int64_t cols = item_count(dims, N, VX, (int)N);   // items of one full-length chunk
+  const int64_t n = cols * nz;
+  // 3D items run z-chunk by z-chunk (the short last chunk at the end), 2D items column by column
+  auto planes = [&](int64_t k) -> double {
+    const bool tail = dims == 3 ? k >= cols * (nz - 1) : (k % nz) == nz - 1;
+    return (double)((tail ? last : Lc) + 2 + 2);
+  };
+  constexpr double kSoloSpeedup = 1.25;
+  std::vector<double> rem;
+  rem.reserve(slots);
+  int64_t next = 0;
+  while (next < n && (int)rem.size() < slots) rem.push_back(planes(next++));
+  double t = 0.0;
+  while (!rem.empty()) {
+    const double rate = std::min(kSoloSpeedup, (double)slots / (double)rem.size());
+    const double m = *std::min_element(rem.begin(), rem.end());
+    t += m / rate;
+    size_t keep = 0;
+    for (size_t i = 0; i < rem.size(); ++i)
+      if (rem[i] - m > 1e-9) rem[keep++] = rem[i] - m;
+    size_t freed = rem.size() - keep;
+    rem.resize(keep);
+    for (; freed > 0 && next < n; --freed) rem.push_back(planes(next++));
+  }
+  return t;
+}
+
+// Item length of a lattice alone: the candidate with the least predicted time
+// (ties to the longer item).  1D lattices are one row; their items do not depend on it.
+int rows_item_length(int dims, int64_t N, int VX, int slots) {
+  static const int kCand[] = {128, 96, 64, 48, 32, 24, 16, 12, 8, 4};
+  if (dims == 1) return 128;
+  int best = 128;
+  double best_t = -1.0;
+  for (int L : kCand) {
+    if (L > N && L != 128) continue;
+    const double t = rows_predicted_time(dims, N, VX, L, slots);
+    if (best_t < 0.0 || t < best_t * (1.0 - 1e-3)) {
+      best_t = t;
+      best = L;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
 // A private one-lattice batch that lets ce_step run the batched kernel on a
 // single handle (lattices the z-sweep kernel does not cover).  It works on the
 // handle's own stream, with step parity given per launch, and does not make
@@ -868,8 +936,7 @@ int ce::rows_create(ce_sim* s, ce_batch** out) {
     return bcuda(e, "ce_create: row-kernel scratch");
   }
   b->d_done = b->d_queue + 2;
-  // item length: the longest (of 128, 64, ..., 4 sites) that still gives two
-  // waves of items, so that one lattice alone fills the GPU
+  // item length along the sweep axis: the candidate the launch model prefers
   int per_sm = 0, sms = 0;
   e = batch_prepare(b->prec, b->nf, &per_sm);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -878,13 +945,7 @@ int ce::rows_create(ce_sim* s, ce_batch** out) {
     delete b;
     return bcuda(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "ce_create: row-kernel occupancy");
   }
-  {
-    const int VX = 16 / s->esize;
-    for (int L = 128; L >= 4; L /= 2) {
-      b->sweep_len = L;
-      if (item_count(s->dims, s->N, VX, L) >= 2LL * per_sm * sms) break;
-    }
-  }
+  b->sweep_len = rows_item_length(s->dims, s->N, 16 / s->esize, per_sm * sms);
   const int cur = s->cur;
   s->cur = 0;   // member parity 0: the launch's parity argument is the input buffer set
   int rc = b->prec == CE_F32 ? upload_tables<float>(b) : upload_tables<double>(b);

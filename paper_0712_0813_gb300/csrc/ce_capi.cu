@@ -31,6 +31,14 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
+// Smallest sides for which the automatic choice takes the row kernel, from
+// timings of both kernels on single lattices: below them a lattice is a few
+// microseconds of traffic and the generic kernel starts faster; FP64 lattices
+// are bound by the FP64 rate in both kernels, and the row kernel pulls ahead
+// only once its longer items amortise their halo planes.
+constexpr int kRowsMinN3F32 = 64;
+constexpr int kRowsMinN3F64 = 256;
+constexpr int kRowsMinN2 = 512;
 constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device-side wait
 
@@ -318,12 +326,15 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   s->dx = cfg->L / (double)cfg->N;
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
+  // automatic choice: the z-sweep kernel where it applies, else the row kernel
+  // for 2D and 3D lattices it takes, else the generic kernel (1D lattices, odd
+  // sides; on a 1D lattice the row kernel's items are single row segments)
+  const int rows_min_n = cfg->dims == 3 ? (cfg->precision == CE_F32 ? kRowsMinN3F32 : kRowsMinN3F64) : kRowsMinN2;
+  const bool rows_auto = rows_ok && cfg->dims >= 2 && cfg->N >= rows_min_n;
   if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
   else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
-  else s->kernel = sweep_ok ? CE_KERNEL_SWEEP : CE_KERNEL_GENERIC;
-  // (the row kernel is not an automatic choice: on one lattice alone it measured
-  //  slower than the generic kernel for every shape tried; it pays off across
-  //  the many long items of a batch)
+  else if (sweep_ok) s->kernel = CE_KERNEL_SWEEP;
+  else s->kernel = rows_auto ? CE_KERNEL_ROWS : CE_KERNEL_GENERIC;
   s->generic_blocks = ce::generic_blocks(S);
   cudaGetDevice(&s->device);
   if (cfg->stream) {
@@ -376,8 +387,13 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   if (s->kernel == CE_KERNEL_ROWS) {
     rc = ce::rows_create(s, &s->rows);
     if (rc != CE_OK) {
-      ce_free(s);
-      return rc;
+      if (cfg->kernel == CE_KERNEL_ROWS) {
+        ce_free(s);
+        return rc;
+      }
+      cudaGetLastError();
+      g_err.clear();
+      s->kernel = CE_KERNEL_GENERIC;   // automatic choice: fall back to the generic kernel
     }
   }
   e = cudaMemsetAsync(s->aux, 0, sizeof(ce::DevAux), s->stream);

@@ -26,32 +26,88 @@ int generic_blocks(int64_t S) {
   return (int)(want < cap ? want : cap);
 }
 
+// Lattice coordinates along a grid-stride walk s0, s0 + stride, ...: one
+// division by N per thread at the start, then additions with carries, so that
+// no site pays for a 64-bit division (the row-major index is s = x + N (y + N z)).
+template <int DIMS>
+struct SiteWalk {
+  int64_t x, y, z;      // coordinates of the current site
+  int64_t dx, dy, dz;   // the stride in coordinates (each < N, except 1D)
+  __device__ __forceinline__ void init(int64_t s0, int64_t stride, int64_t N) {
+    y = z = dy = dz = 0;
+    if (DIMS == 1) {   // x = s: nothing to wrap inside the walk (s < S = N)
+      x = s0;
+      dx = stride;
+      return;
+    }
+    x = s0 % N;
+    dx = stride % N;
+    const int64_t r = s0 / N, dr = stride / N;
+    if (DIMS == 2) {
+      y = r;
+      dy = dr;
+    } else {
+      y = r % N;
+      z = r / N;
+      dy = dr % N;
+      dz = dr / N;
+    }
+  }
+  // x + dx < 2N and y + dy + 1 < 2N: one conditional subtraction each.  y (2D)
+  // and z (3D) leave [0, N) only once the walk has passed the last site.
+  __device__ __forceinline__ void advance(int64_t N) {
+    x += dx;
+    if (DIMS == 1) return;
+    int64_t carry = 0;
+    if (x >= N) {
+      x -= N;
+      carry = 1;
+    }
+    y += dy + carry;
+    if (DIMS == 3) {
+      carry = 0;
+      if (y >= N) {
+        y -= N;
+        carry = 1;
+      }
+      z += dz + carry;
+    }
+  }
+};
+
+// The 2 DIMS nearest neighbours of site s at (x, y, z), periodic wrap:
+// nb[2d] = s + e_d, nb[2d+1] = s - e_d.
+template <int DIMS>
+__device__ __forceinline__ void neighbours(int64_t s, const SiteWalk<DIMS>& c, int64_t N, int64_t (&nb)[2 * DIMS]) {
+  nb[0] = (c.x == N - 1) ? s - (N - 1) : s + 1;
+  nb[1] = (c.x == 0) ? s + (N - 1) : s - 1;
+  if (DIMS >= 2) {
+    nb[2] = (c.y == N - 1) ? s - (N - 1) * N : s + N;
+    nb[3] = (c.y == 0) ? s + (N - 1) * N : s - N;
+  }
+  if (DIMS >= 3) {
+    const int64_t NN = N * N;
+    nb[4] = (c.z == N - 1) ? s - (N - 1) * NN : s + NN;
+    nb[5] = (c.z == 0) ? s + (N - 1) * NN : s - NN;
+  }
+}
+
 template <typename T, int NF, int DIMS>
 __global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs<T> p) {
   const T c = (T)p.sc_in->c;
   const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
-  const int64_t N = p.N, S = p.S, NN = N * N;
+  const int64_t N = p.N, S = p.S;
   T q[3] = {p.q[0], p.q[1], p.q[2]};
   double grad2 = 0.0, pot = 0.0;   // flushed from the T partials every 16 sites
   T g2loc = T(0), vloc = T(0);
   int since_flush = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += stride) {
-    const int64_t x = s % N;
-    const int64_t r = s / N;
+  const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  SiteWalk<DIMS> at;
+  at.init(s0, stride, N);
+  for (int64_t s = s0; s < S; s += stride, at.advance(N)) {
     int64_t nb[2 * DIMS];
-    nb[0] = (x == N - 1) ? s - (N - 1) : s + 1;
-    nb[1] = (x == 0) ? s + (N - 1) : s - 1;
-    if (DIMS >= 2) {
-      const int64_t y = (DIMS == 2) ? r : r % N;
-      nb[2] = (y == N - 1) ? s - (N - 1) * N : s + N;
-      nb[3] = (y == 0) ? s + (N - 1) * N : s - N;
-    }
-    if (DIMS >= 3) {
-      const int64_t z = r / N;
-      nb[4] = (z == N - 1) ? s - (N - 1) * NN : s + NN;
-      nb[5] = (z == 0) ? s + (N - 1) * NN : s - NN;
-    }
+    neighbours<DIMS>(s, at, N, nb);
     T g[NF], v[NF], lap[NF];
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
@@ -124,23 +180,10 @@ template cudaError_t launch_step_generic<double>(const StepArgs<double>&, int, c
 // With raw_u (start-up input) u is w itself.
 
 template <typename T, int NF, int DIMS>
-__device__ __forceinline__ void site_u(const DiagArgs<T>& p, int64_t s, double (&fv)[NF],
-                                       double (&u)[NF], double (&g2)[NF]) {
-  const int64_t N = p.N, NN = N * N;
-  const int64_t x = s % N, r = s / N;
+__device__ __forceinline__ void site_u(const DiagArgs<T>& p, int64_t s, const SiteWalk<DIMS>& at,
+                                       double (&fv)[NF], double (&u)[NF], double (&g2)[NF]) {
   int64_t nb[2 * DIMS];
-  nb[0] = (x == N - 1) ? s - (N - 1) : s + 1;
-  nb[1] = (x == 0) ? s + (N - 1) : s - 1;
-  if (DIMS >= 2) {
-    const int64_t y = (DIMS == 2) ? r : r % N;
-    nb[2] = (y == N - 1) ? s - (N - 1) * N : s + N;
-    nb[3] = (y == 0) ? s + (N - 1) * N : s - N;
-  }
-  if (DIMS >= 3) {
-    const int64_t z = r / N;
-    nb[4] = (z == N - 1) ? s - (N - 1) * NN : s + NN;
-    nb[5] = (z == 0) ? s + (N - 1) * NN : s - NN;
-  }
+  neighbours<DIMS>(s, at, p.N, nb);
   double lap[NF];
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
@@ -187,9 +230,12 @@ __global__ void __launch_bounds__(256) k_diag(const DiagArgs<T> p) {
 #pragma unroll
   for (int i = 0; i < NF; ++i) shift[i] = (double)p.f[i][0];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < p.S; s += stride) {
+  const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  SiteWalk<DIMS> at;
+  at.init(s0, stride, p.N);
+  for (int64_t s = s0; s < p.S; s += stride, at.advance(p.N)) {
     double fv[NF], u[NF], g2[NF];
-    site_u<T, NF, DIMS>(p, s, fv, u, g2);
+    site_u<T, NF, DIMS>(p, s, at, fv, u, g2);
     double dv[NF], vs;
     double q[3] = {p.q[0], p.q[1], p.q[2]};
     model_dv<double, NF>(fv, q, dv, vs);
@@ -218,17 +264,20 @@ __global__ void __launch_bounds__(256) k_diag(const DiagArgs<T> p) {
   }
 }
 
-// One block: combine the diag partials in block order and derive the outputs.
+// One block of one warp per quantity: combine the diag partials (lane l takes
+// blocks l, l + 32, ..., then a fixed shuffle tree) and derive the outputs.
 template <int NF>
 __global__ void k_diag_finalize(const double* partials, int blocks, DevAux* aux, int64_t S,
                                 double half_inv_dx2, double dt, double kappa2, int expansion,
                                 const DevScalars* sc) {
   constexpr int NV = 4 * NF + 1;
   __shared__ double tot[NV];
-  if (threadIdx.x < NV) {
+  const int lane = threadIdx.x & 31;
+  for (int k = threadIdx.x >> 5; k < NV; k += blockDim.x >> 5) {
     double t = 0.0;
-    for (int b = 0; b < blocks; ++b) t += partials[(int64_t)b * NV + threadIdx.x];
-    tot[threadIdx.x] = t;
+    for (int b = lane; b < blocks; b += 32) t += partials[(int64_t)b * NV + k];
+    t = warp_sum(t);
+    if (lane == 0) tot[k] = t;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -270,10 +319,13 @@ __global__ void k_mean_shift(DevAux* aux, const T* f0, const T* f1, const T* f2,
 template <typename T, int NF, int DIMS>
 __global__ void __launch_bounds__(256) k_sync_u_range(const DiagArgs<T> p) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.count; k += stride) {
+  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  SiteWalk<DIMS> at;
+  at.init(p.s0 + k0, stride, p.N);
+  for (int64_t k = k0; k < p.count; k += stride, at.advance(p.N)) {
     const int64_t s = p.s0 + k;
     double fv[NF], u[NF], g2[NF];
-    site_u<T, NF, DIMS>(p, s, fv, u, g2);
+    site_u<T, NF, DIMS>(p, s, at, fv, u, g2);
 #pragma unroll
     for (int i = 0; i < NF; ++i) p.u_out[(int64_t)i * p.count + k] = u[i];
   }
@@ -289,7 +341,7 @@ static cudaError_t launch_diag_nf(const DiagArgs<T>& a, int blocks, cudaStream_t
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const double dx2inv = a.inv_dx2;
-  k_diag_finalize<NF><<<1, 64, 0, st>>>(a.partials, blocks, a.aux, a.S, 0.5 * dx2inv, a.dt, a.kappa2,
+  k_diag_finalize<NF><<<1, 32 * (4 * NF + 1), 0, st>>>(a.partials, blocks, a.aux, a.S, 0.5 * dx2inv, a.dt, a.kappa2,
                                          a.expansion, a.sc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

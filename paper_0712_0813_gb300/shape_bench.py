@@ -6,7 +6,8 @@
   and its 1D, 2D and 3D parts alone, one ``k_step_batched`` launch per step;
 * ``batch_3d``: homogeneous batches of about 100 M sites of one 3D side;
 * ``single``: one lattice stepped by ``ce_step`` with the generic kernel and
-  with the row kernel (``CE_KERNEL_ROWS``).
+  with the row kernel (``CE_KERNEL_ROWS``, the automatic choice for 2D sides
+  >= 512 and 3D sides >= 64 (FP32) / 256 (FP64) outside the z-sweep kernel).
 
 Times are CUDA events on the library's stream around ``steps`` steps after
 ``warmup`` steps (graphs of 32 launches); ``frac`` is the algorithmic 16 B per
@@ -96,8 +97,9 @@ def run(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> list:
         print(json.dumps(row), flush=True)
         for s in sims:
             s.close()
-    for dims, N in ((1, 65536), (2, 1024), (3, 64), (3, 96), (3, 160), (3, 192)):
-        f0, u0 = lattice_ics(dims, N, 20.0, 2, q=(1.2,), seed=3, amp=1e-2)
+    for dims, N in ((1, 65536), (2, 1024), (2, 6000), (3, 64), (3, 96), (3, 160), (3, 192), (3, 288), (3, 448)):
+        big = N ** dims >= 1 << 22
+        f0, u0 = lattice_ics(dims, N, 20.0, 2, q=(1.2,), seed=3, amp=1e-2, backend="torch" if big else "numpy")
         dt = courant_dt(dims, N, 20.0, 1.0, (1.2,))
         row = {"case": "single", "dims": dims, "N": N}
         for prec in ("f32", "f64"):
@@ -105,7 +107,8 @@ def run(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> list:
                 with capi.Simulation(dims=dims, N=N, L=20.0, dt=dt, nfields=2, q=(1.2,), expansion=True,
                                      precision=prec, kernel=kern, stream=stream.cuda_stream) as s:
                     s.set_fields(f0, u0)
-                    row[f"{prec}_{kern}_us"] = _timed(torch, stream, s.step, 2 * steps, 2 * warmup)
+                    n = max(10, min(2 * steps, int(2e9 / (N ** dims * 8 * (4 if prec == "f32" else 8)))))
+                    row[f"{prec}_{kern}_us"] = _timed(torch, stream, s.step, n, min(2 * warmup, n))
         rows.append(row)
         print(json.dumps(row), flush=True)
     return rows

@@ -63,11 +63,17 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", ["auto", "generic"])
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d_N{c[1]}_nf{c[4]}_{'exp' if c[6] else 'flat'}" for c in CASES])
-def test_fp64_parity_100_steps(gpu_capi, orc, case):
+def test_fp64_parity_100_steps(gpu_capi, orc, case, kernel):
+    """The automatic kernel choice, and the generic kernel where that choice is
+    another kernel, against the oracle."""
     dims, N, L, dt, nf, q, expansion = case
-    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, expansion, 100)
+    if kernel == "generic" and auto_kernel(gpu_capi, dims, N, "f64") == gpu_capi.CE_KERNEL_GENERIC:
+        pytest.skip("the automatic choice is the generic kernel")
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, expansion, 100, kernel=kernel)
     with sim:
+        assert sim.kernel == (auto_kernel(gpu_capi, dims, N, "f64") if kernel == "auto" else gpu_capi.CE_KERNEL_GENERIC)
         assert per_field_err(f, ref.f, nf) <= TOL64
         assert per_field_err(v, ref.v, nf) <= TOL64
         assert sc.step == 100 and sc.t == ref.scale.t
@@ -289,10 +295,25 @@ def test_sweep_variants_fp32_vs_oracle(gpu_capi, orc, rows, stages):
     assert per_field_err(v, ref.v, nf) <= 2e-5
 
 
-@pytest.mark.parametrize("dims,N,precision", [(3, 96, "f64"), (2, 130, "f64"), (1, 2048, "f64"), (3, 40, "f32")])
+def auto_kernel(capi, dims, N, precision):
+    """The kernel ce_create picks by itself: the z-sweep kernel for 3D sides that
+    are multiples of its tile, the row kernel for other 2D/3D lattices that it
+    takes with sides >= 64 (3D FP32), 256 (3D FP64) or 512 (2D), the generic
+    kernel for the rest."""
+    if dims == 3 and N % (128 if precision == "f32" else 64) == 0:
+        return capi.CE_KERNEL_SWEEP
+    min_n = (64 if precision == "f32" else 256) if dims == 3 else 512
+    if dims >= 2 and N % (4 if precision == "f32" else 2) == 0 and N >= min_n:
+        return capi.CE_KERNEL_ROWS
+    return capi.CE_KERNEL_GENERIC
+
+
+@pytest.mark.parametrize("dims,N,precision", [(3, 96, "f64"), (2, 130, "f64"), (1, 2048, "f64"), (3, 40, "f32"),
+                                              (3, 68, "f32"), (2, 520, "f32")])
 def test_row_kernel_single_lattice(gpu_capi, orc, dims, N, precision):
     """ce_step through the batched row-sweep kernel on one lattice (CE_KERNEL_ROWS,
-    an explicit choice) against the oracle."""
+    an explicit choice) against the oracle; the item length along the sweep axis
+    is the one ce_create's launch model picks for the lattice."""
     q, nf = (1.2,), 2
     dt = 0.02 if dims > 1 else 0.004
     ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, 20.0, dt, nf, q, True, 40, precision=precision,
@@ -303,5 +324,4 @@ def test_row_kernel_single_lattice(gpu_capi, orc, dims, N, precision):
         assert per_field_err(f, ref.f, nf) <= tol_f
         assert per_field_err(v, ref.v, nf) <= tol_v
     with gpu_capi.Simulation(dims=dims, N=N, L=20.0, dt=dt, nfields=nf, q=q, precision=precision) as auto:
-        assert auto.kernel == (gpu_capi.CE_KERNEL_SWEEP if (dims == 3 and N % (128 if precision == "f32" else 64) == 0)
-                               else gpu_capi.CE_KERNEL_GENERIC)
+        assert auto.kernel == auto_kernel(gpu_capi, dims, N, precision)
