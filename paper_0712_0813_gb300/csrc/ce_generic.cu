@@ -151,10 +151,121 @@ __global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs
   }
 }
 
+// 16 bytes of consecutive sites: VX = 16 / sizeof(T) values, one vector access.
+template <typename T, int VX>
+__device__ __forceinline__ void ldg16(const T* p, T (&o)[VX]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+}
+template <typename T, int VX>
+__device__ __forceinline__ void stcs16(T* p, const T (&o)[VX]) {
+  if constexpr (sizeof(T) == 4) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
+  } else {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+  }
+}
+
+// The 1D step for N a multiple of VX = 16 / sizeof(T): each thread takes VX
+// consecutive sites with 16-byte loads and stores, and the sites on either side
+// of them (periodic wrap) with scalar loads that the neighbouring threads'
+// vectors already brought into L1.  Each site's g is formed once per field and
+// shared by its two neighbours.  Per site the arithmetic is that of
+// k_step_generic (same operations in the same order), so the fields agree bit
+// for bit; the block sums are added in another order.
+template <typename T, int NF>
+__global__ void __launch_bounds__(kGenericThreads) k_step_1d(const StepArgs<T> p) {
+  constexpr int VX = 16 / sizeof(T);
+  const T c = (T)p.sc_in->c;
+  const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
+  const int64_t N = p.N, groups = N / VX;
+  T q[3] = {p.q[0], p.q[1], p.q[2]};
+  double grad2 = 0.0, pot = 0.0;   // flushed from the T partials every 4 groups
+  T g2loc = T(0), vloc = T(0);
+  int since_flush = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < groups; k += stride) {
+    const int64_t s = k * VX;
+    const int64_t sl = (k == 0) ? N - 1 : s - 1;             // left neighbour of the first site
+    const int64_t sr = (k == groups - 1) ? 0 : s + VX;       // right neighbour of the last site
+    T g[NF][VX + 2], v[NF][VX];   // g[i][1 + j] at site s + j; [0] and [VX + 1] the outer neighbours
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      T f[VX], w[VX];
+      ldg16<T, VX>(p.f_in[i] + s, f);
+      ldg16<T, VX>(p.w_in[i] + s, w);
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        v[i][j] = fmaT(c, f[j], w[j]);
+        g[i][j + 1] = fmaT(dd, v[i][j], f[j]);
+      }
+      const T fl = __ldg(p.f_in[i] + sl), wl = __ldg(p.w_in[i] + sl);
+      const T fr = __ldg(p.f_in[i] + sr), wr = __ldg(p.w_in[i] + sr);
+      g[i][0] = fmaT(dd, fmaT(c, fl, wl), fl);
+      g[i][VX + 1] = fmaT(dd, fmaT(c, fr, wr), fr);
+    }
+    T wo[NF][VX], fo[NF][VX];
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+      T gs[NF], lap[NF];
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const T gc = g[i][j + 1], gp = g[i][j + 2], gm = g[i][j];
+        T acc = T(0);
+        acc += (gp + gm) - T(2) * gc;
+        const T df = gp - gc;
+        g2loc = fmaT(df, df, g2loc);
+        lap[i] = acc * idx2;
+        gs[i] = gc;
+      }
+      T dv[NF], vs;
+      model_dv<T, NF>(gs, q, dv, vs);
+      vloc += vs;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        wo[i][j] = fmaT(kk, lap[i] - dv[i], v[i][j]);
+        fo[i][j] = gs[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      stcs16<T, VX>(p.w_out[i] + s, wo[i]);
+      stcs16<T, VX>(p.f_out[i] + s, fo[i]);
+    }
+    since_flush += VX;
+    if (since_flush >= 16) {
+      grad2 += (double)g2loc;
+      pot += (double)vloc;
+      g2loc = T(0);
+      vloc = T(0);
+      since_flush = 0;
+    }
+  }
+  if (p.update_scalars) {
+    grad2 += (double)g2loc;
+    pot += (double)vloc;
+    finish_step_block(p, grad2, pot);
+  }
+}
+
 template <typename T, int NF>
 static cudaError_t launch_generic_nf(const StepArgs<T>& a, int blocks, cudaStream_t st) {
+  constexpr int VX = 16 / sizeof(T);
   switch (a.dims) {
-    case 1: k_step_generic<T, NF, 1><<<blocks, kGenericThreads, 0, st>>>(a); break;
+    case 1:
+      if (a.N % VX == 0) {
+        const int64_t want = (a.N / VX + kGenericThreads - 1) / kGenericThreads;
+        const int b1 = (int)(want < blocks ? want : blocks);
+        k_step_1d<T, NF><<<b1 < 1 ? 1 : b1, kGenericThreads, 0, st>>>(a);
+      } else {
+        k_step_generic<T, NF, 1><<<blocks, kGenericThreads, 0, st>>>(a);
+      }
+      break;
     case 2: k_step_generic<T, NF, 2><<<blocks, kGenericThreads, 0, st>>>(a); break;
     default: k_step_generic<T, NF, 3><<<blocks, kGenericThreads, 0, st>>>(a); break;
   }

@@ -33,6 +33,7 @@ import numpy as np
 import pytest
 
 from paper_0712_0813_gb300.icgen import courant_dt, lattice_ics
+from step_bounds import check_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -59,42 +60,6 @@ def plan_sites(N, tx, ty, zchunks, n_random=3000, seed=11):
     rng = np.random.default_rng(seed)
     rand = rng.integers(0, N ** 3, size=n_random)
     return np.unique(np.concatenate([edges, rand]).astype(np.int64))
-
-
-EPS32 = 2.0 ** -24   # unit roundoff of FP32 storage
-
-
-def check_one_step(orc, local, p, before, after, sites, stencil, G, V):
-    """before/after: (f, v, scalars) sampled at stencil / sites.
-
-    Error bound of one FP32 step against FP64 arithmetic on the same stored
-    inputs (the oracle starts from the sampled FP32 values, so only the step's
-    own roundings count): f' = g = f + dt v is one rounding of |f| + dt |v|;
-    v' = v + dt (lap g - dV/df(g) + s g) carries the rounding of every g it
-    reads multiplied by the Laplacian's weights (sum 4 d / dx^2), of dV/df and
-    of the sum, each a few units of EPS32.  Eight units per term leave room
-    for the FMA/non-FMA differences and the final conversions."""
-    fb, vb, scb = before
-    fa, va, sca = after
-    ref = local.step_at(p, sites, stencil, fb, vb, scb.a, scb.ap_half, G, V)
-    dxinv2 = (p.N / p.L) ** 2
-    s = ref.app / ref.a
-    q = list(p.q) + [0.0] * 3
-    gm = [float(np.abs(ref.f[i]).max()) for i in range(p.nf)]
-    # |dV/df_i| bounds: phi^3 + phi sum q chi^2, and q_i phi^2 chi_i
-    dvm = [gm[0] ** 3 + gm[0] * sum(q[j - 1] * gm[j] ** 2 for j in range(1, p.nf))]
-    dvm += [q[i - 1] * gm[0] ** 2 * gm[i] for i in range(1, p.nf)]
-    for i in range(p.nf):
-        vmax = float(np.abs(vb[i]).max())
-        tol_f = 4.0 * EPS32 * (float(np.abs(fb[i]).max()) + p.dt * vmax)
-        tol_v = 8.0 * EPS32 * (vmax + p.dt * ((4 * p.dims + 2) * dxinv2 * gm[i] + dvm[i] + abs(s) * gm[i]))
-        assert np.abs(fa[i] - ref.f[i]).max() <= tol_f, (i, np.abs(fa[i] - ref.f[i]).max(), tol_f)
-        assert np.abs(va[i] - ref.v[i]).max() <= tol_v, (i, np.abs(va[i] - ref.v[i]).max(), tol_v)
-    assert abs(sca.a - ref.a) <= 1e-12 * ref.a
-    Q = p.kappa2 * (2.0 * G + 3.0 * V) / ref.a
-    scale = abs(Q) + ref.ap ** 2 / ref.a
-    assert abs(sca.app - ref.app) <= 1e-5 * scale
-    assert abs(sca.ap_half - ref.ap) <= 1e-5 * p.dt * scale + 1e-12 * abs(ref.ap)
 
 
 SINGLE = [

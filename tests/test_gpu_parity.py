@@ -14,7 +14,8 @@ import math
 import numpy as np
 import pytest
 
-from paper_0712_0813_gb300.icgen import lattice_ics
+from paper_0712_0813_gb300.icgen import courant_dt, lattice_ics
+from step_bounds import check_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -293,6 +294,45 @@ def test_sweep_variants_fp32_vs_oracle(gpu_capi, orc, rows, stages):
         f, v, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
     assert per_field_err(f, ref.f, nf) <= 2e-6
     assert per_field_err(v, ref.v, nf) <= 2e-5
+
+
+@pytest.mark.parametrize("N,nf,precision", [(4096, 1, "f64"), (4096, 4, "f64"), (1001, 2, "f64"), (8, 3, "f64"),
+                                          (65536, 2, "f64"), (4, 2, "f32"), (4096, 2, "f32"), (65536, 2, "f32")])
+def test_1d_kernel_vs_oracle(gpu_capi, orc, N, nf, precision):
+    """1D lattices on the generic path: sides that are multiples of the 16-byte
+    vector take the vectorised 1D kernel (down to a single vector of sites, whose
+    two neighbours wrap onto itself), other sides the one-thread-per-site kernel.
+    FP64: 40 steps against the oracle.  FP32: after 20 steps, one step from the
+    exported state at every site within the derived FP32 one-step bound (over
+    many steps FP32 storage drifts from the FP64 oracle whatever the kernel: on
+    the 65536-site lattice the Laplacian's 1/dx^2 ~ 1e7 weight makes that ~1e-3
+    of v in 40 steps)."""
+    from oracle import local
+    q = (0.8, 5.0, 40.0)[: nf - 1]
+    L = 20.0
+    dt = courant_dt(1, N, L, 1.0, q)
+    f0, u0 = lattice_ics(1, N, L, nf, q=q, seed=1, amp=1e-2)
+    p = orc.Params(dims=1, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
+    with gpu_capi.Simulation(dims=1, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision=precision,
+                             kernel="generic") as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_GENERIC
+        sim.set_fields(f0, u0)
+        if precision == "f64":
+            ref = orc.step(orc.init(p, f0, u0), 40)
+            sim.step(40)
+            f, v, sc = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+            assert per_field_err(f, ref.f, nf) <= TOL64
+            assert per_field_err(v, ref.v, nf) <= TOL64
+            assert abs(sc.a - ref.scale.a) <= 1e-12 * ref.scale.a
+        else:
+            sim.step(20)
+            sites = np.arange(N, dtype=np.int64)
+            stencil = local.stencil_sites(1, N, sites)
+            before = sim.sample_fields(stencil)
+            sim.step(1)
+            after = sim.sample_fields(sites)
+            en = sim.energy()
+            check_one_step(orc, local, p, before, after, sites, stencil, float(np.sum(en["G"])), en["V"])
 
 
 def auto_kernel(capi, dims, N, precision):
