@@ -252,7 +252,14 @@ def test_full_size_256cube_one_step_against_oracle(gpu_capi, orc, precision, tol
     assert per_field_err(f1, st.f, nf) <= tol_f
     assert per_field_err(v1, st.v, nf) <= tol_v
     assert abs(sc1.a - st.scale.a) <= 1e-12 * st.scale.a
-    assert abs(sc1.ap_half - st.scale.ap) <= 1e-9 * abs(st.scale.ap)
+    if precision == "f64":
+        assert abs(sc1.ap_half - st.scale.ap) <= 1e-9 * abs(st.scale.ap)
+    else:
+        # G and V come from FP32 per-thread partial sums (folded into FP64 per
+        # block): a'' is good to ~1e-5 of its source term Q, |Q| <= |a''| + a'^2/a,
+        # so one step moves a' by at most 1e-5 dt of that (the full-size tests' bound)
+        scale = abs(st.scale.app) + st.scale.ap ** 2 / st.scale.a
+        assert abs(sc1.ap_half - st.scale.ap) <= 1e-5 * dt * scale + 1e-12 * abs(st.scale.ap)
 
 
 VARIANTS = [(8, 4), (8, 5), (16, 3), (16, 4), (4, 4), (4, 5)]
@@ -279,6 +286,17 @@ def test_sweep_variants_and_directions_match_generic_fp64(gpu_capi, rows, stages
     assert per_field_err(out["sweep"][0], out["generic"][0], nf) <= 1e-12
     assert per_field_err(out["sweep"][1], out["generic"][1], nf) <= 1e-12
     assert abs(out["sweep"][2].a - out["generic"][2].a) <= 1e-13 * out["generic"][2].a
+
+
+def test_automatic_plan_of_the_256cube_lattice(gpu_capi):
+    """Without hints the bench lattice (3D 256^3, 2 fields, FP32) gets the plan the
+    autotuner measures fastest on a GB300 (152 SMs): 8 rows, 4 stages, 4
+    z-chunks, 0.84 of a wave of 304 CTAs, which the launch model prefers to the
+    14 chunks that would fill whole waves (101.6 against 93.3 us per step)."""
+    with gpu_capi.Simulation(dims=3, N=256, L=20.0, dt=0.02, nfields=2, q=(1.2,), expansion=True,
+                             precision="f32") as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
+        assert sim.sweep_plan == (8, 4, 4)
 
 
 @pytest.mark.parametrize("rows,stages", VARIANTS)
