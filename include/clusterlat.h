@@ -69,9 +69,11 @@ extern "C" {
                                with ce_scalars_t this is a complete state    */
 
 /* ---- kernel selection (ce_config.kernel) ------------------------------ */
-#define CE_KERNEL_AUTO    0 /* z-sweep kernel where it applies; else the row
-                               kernel for 2D sides >= 512 and 3D sides >= 64
-                               (FP32) / 256 (FP64) it takes; else generic    */
+#define CE_KERNEL_AUTO    0 /* FP32: z-sweep kernel where it applies; else the
+                               row kernel for 2D sides >= 512 and 3D sides >= 64
+                               it takes; else generic.  FP64: generic (its
+                               two-pass form), or the z-sweep kernel when plan
+                               hints (tile_rows, stages, zchunks) are given    */
 #define CE_KERNEL_GENERIC 1 /* one thread per site, any d and N              */
 #define CE_KERNEL_SWEEP   2 /* 3D z-sweep kernel (CE_EINVAL if it does not apply) */
 #define CE_KERNEL_ROWS    3 /* the batched row-sweep kernel on this one lattice:

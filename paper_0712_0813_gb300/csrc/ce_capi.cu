@@ -31,13 +31,10 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
-// Smallest sides for which the automatic choice takes the row kernel, from
-// timings of both kernels on single lattices: below them a lattice is a few
-// microseconds of traffic and the generic kernel starts faster; FP64 lattices
-// are bound by the FP64 rate in both kernels, and the row kernel pulls ahead
-// only once its longer items amortise their halo planes.
-constexpr int kRowsMinN3F32 = 64;
-constexpr int kRowsMinN3F64 = 256;
+// Smallest sides for which the automatic choice takes the row kernel (FP32),
+// from timings of both kernels on single lattices: below them a lattice is a
+// few microseconds of traffic and the generic kernel starts faster.
+constexpr int kRowsMinN3 = 64;
 constexpr int kRowsMinN2 = 512;
 constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device-side wait
@@ -326,14 +323,20 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   s->dx = cfg->L / (double)cfg->N;
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
-  // automatic choice: the z-sweep kernel where it applies, else the row kernel
-  // for 2D and 3D lattices it takes, else the generic kernel (1D lattices, odd
-  // sides; on a 1D lattice the row kernel's items are single row segments)
-  const int rows_min_n = cfg->dims == 3 ? (cfg->precision == CE_F32 ? kRowsMinN3F32 : kRowsMinN3F64) : kRowsMinN2;
-  const bool rows_auto = rows_ok && cfg->dims >= 2 && cfg->N >= rows_min_n;
+  // Automatic choice.  FP32: the z-sweep kernel where it applies, else the row
+  // kernel for 2D and 3D lattices it takes, else the generic kernel (1D
+  // lattices, odd and small sides).  FP64 is bound by the FP64 rate, and there
+  // the generic kernel's two-pass form (each site's g formed once) measured
+  // faster than both the z-sweep kernel (256^3: 1090 against 1141 us, tuned
+  // plan) and the row kernel (288^3: 1540 against 2967 us): the generic kernel,
+  // unless the caller gave z-sweep plan hints.
+  const bool sweep_hinted = cfg->tile_rows != 0 || cfg->stages != 0 || cfg->zchunks != 0;
+  const bool rows_auto = rows_ok && cfg->precision == CE_F32 && cfg->dims >= 2 &&
+                         cfg->N >= (cfg->dims == 3 ? kRowsMinN3 : kRowsMinN2);
   if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
   else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
-  else if (sweep_ok) s->kernel = CE_KERNEL_SWEEP;
+  else if (sweep_ok && (cfg->precision == CE_F32 || sweep_hinted || cfg->kernel == CE_KERNEL_SWEEP))
+    s->kernel = CE_KERNEL_SWEEP;
   else s->kernel = rows_auto ? CE_KERNEL_ROWS : CE_KERNEL_GENERIC;
   s->generic_blocks = ce::generic_blocks(S);
   cudaGetDevice(&s->device);

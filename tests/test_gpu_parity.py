@@ -239,7 +239,7 @@ def test_full_size_256cube_one_step_against_oracle(gpu_capi, orc, precision, tol
     N, nf, q, dt, L = 256, 2, (1.2,), 0.02, 20.0
     f0, u0 = lattice_ics(3, N, L, nf, q=q, seed=1)
     with gpu_capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True,
-                             precision=precision) as sim:
+                             precision=precision, kernel="sweep") as sim:
         assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
         sim.set_fields(f0, u0)
         sim.step(20)
@@ -354,14 +354,15 @@ def test_1d_kernel_vs_oracle(gpu_capi, orc, N, nf, precision):
 
 
 def auto_kernel(capi, dims, N, precision):
-    """The kernel ce_create picks by itself: the z-sweep kernel for 3D sides that
-    are multiples of its tile, the row kernel for other 2D/3D lattices that it
-    takes with sides >= 64 (3D FP32), 256 (3D FP64) or 512 (2D), the generic
-    kernel for the rest."""
-    if dims == 3 and N % (128 if precision == "f32" else 64) == 0:
+    """The kernel ce_create picks by itself (no plan hints).  FP32: the z-sweep
+    kernel for 3D sides that are multiples of its tile, the row kernel for other
+    2D/3D lattices it takes with sides >= 64 (3D) or 512 (2D), the generic kernel
+    for the rest.  FP64: the generic kernel (its two-pass form in 2D/3D)."""
+    if precision == "f64":
+        return capi.CE_KERNEL_GENERIC
+    if dims == 3 and N % 128 == 0:
         return capi.CE_KERNEL_SWEEP
-    min_n = (64 if precision == "f32" else 256) if dims == 3 else 512
-    if dims >= 2 and N % (4 if precision == "f32" else 2) == 0 and N >= min_n:
+    if dims >= 2 and N % 4 == 0 and N >= (64 if dims == 3 else 512):
         return capi.CE_KERNEL_ROWS
     return capi.CE_KERNEL_GENERIC
 
