@@ -156,13 +156,14 @@ __global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs
 // FP64 in 2D and 3D, two passes.  In FP64 the step is bound by GB300's FP64
 // rate, and the one-pass kernel forms g = f + dt (w + c f) again for every
 // neighbour that reads it (2d + 1 times per site).  Pass 1 writes each site's g
-// once, into f_out (which holds g after the step anyway); pass 2 reads the
-// neighbours' g from there, sums the 2d neighbours once and takes the gradient
-// energy by summation by parts on the periodic lattice,
+// once, into f_out (which holds g after the step anyway), and v = w + c f into
+// w_out (which pass 2 overwrites at the same site, in the same thread); pass 2
+// reads the neighbours' g and the site's v from there, sums the 2d neighbours
+// once and takes the gradient energy by summation by parts on the periodic lattice,
 //   sum_x sum_d (g(x+e_d) - g(x))^2 = -sum_x g(x) raw(x),
 //   raw(x) = sum_d (g(x+e_d) + g(x-e_d)) - 2d g(x)
 // (exact in exact arithmetic; the cancellation costs ~1e-12 of G in FP64, which
-// enters only a'').  About 14 FP64 operations per field and site instead of ~33.
+// enters only a'').  About 16 FP64 operations per field and site instead of ~33.
 template <int NF>
 __global__ void __launch_bounds__(kGenericThreads) k_drift_g(const StepArgs<double> p) {
   const double c = p.sc_in->c, dd = p.dt_drift;
@@ -171,14 +172,16 @@ __global__ void __launch_bounds__(kGenericThreads) k_drift_g(const StepArgs<doub
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
       const double f = p.f_in[i][s];
-      p.f_out[i][s] = fma(dd, fma(c, f, p.w_in[i][s]), f);
+      const double v = fma(c, f, p.w_in[i][s]);
+      p.w_out[i][s] = v;
+      p.f_out[i][s] = fma(dd, v, f);
     }
   }
 }
 
 template <int NF, int DIMS>
 __global__ void __launch_bounds__(kGenericThreads) k_kick_from_g(const StepArgs<double> p) {
-  const double c = p.sc_in->c, kk = p.dt_kick, idx2 = p.inv_dx2;
+  const double kk = p.dt_kick, idx2 = p.inv_dx2;
   const int64_t N = p.N, S = p.S;
   double q[3] = {p.q[0], p.q[1], p.q[2]};
   double grad2 = 0.0, pot = 0.0;
@@ -205,10 +208,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_kick_from_g(const StepArgs<
     model_dv<double, NF>(g, q, dv, vs);
     pot += vs;
 #pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      const double v = fma(c, p.f_in[i][s], p.w_in[i][s]);
-      p.w_out[i][s] = fma(kk, lap[i] - dv[i], v);
-    }
+    for (int i = 0; i < NF; ++i) p.w_out[i][s] = fma(kk, lap[i] - dv[i], p.w_out[i][s]);
   }
   if (p.update_scalars) finish_step_block(p, grad2, pot);
 }
