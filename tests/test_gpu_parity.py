@@ -288,6 +288,21 @@ def test_sweep_variants_and_directions_match_generic_fp64(gpu_capi, rows, stages
     assert abs(out["sweep"][2].a - out["generic"][2].a) <= 1e-13 * out["generic"][2].a
 
 
+def test_automatic_choice_in_fp64_and_plan_hints(gpu_capi):
+    """FP64 2D/3D lattices run the generic kernel's two-pass form (measured faster
+    than the z-sweep and row kernels there); z-sweep plan hints select the z-sweep
+    kernel."""
+    kw = dict(dims=3, N=128, L=20.0, dt=0.02, nfields=2, q=(1.2,), expansion=True, precision="f64")
+    with gpu_capi.Simulation(**kw) as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_GENERIC
+        assert sim.sweep_plan == (0, 0, 0)
+    with gpu_capi.Simulation(**kw, tile_rows=8) as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
+        assert sim.sweep_plan[0] == 8
+    with gpu_capi.Simulation(**dict(kw, dims=2, N=1024)) as sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_GENERIC
+
+
 def test_automatic_plan_of_the_256cube_lattice(gpu_capi):
     """Without hints the bench lattice (3D 256^3, 2 fields, FP32) gets the plan the
     autotuner measures fastest on a GB300 (152 SMs): 8 rows, 4 stages, 4
