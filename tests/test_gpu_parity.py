@@ -299,7 +299,7 @@ def test_automatic_choice_in_fp64_and_plan_hints(gpu_capi):
     with gpu_capi.Simulation(**kw, tile_rows=8) as sim:
         assert sim.kernel == gpu_capi.CE_KERNEL_SWEEP
         assert sim.sweep_plan[0] == 8
-    with gpu_capi.Simulation(**dict(kw, dims=2, N=1024)) as sim:
+    with gpu_capi.Simulation(**dict(kw, dims=2, N=1024, dt=courant_dt(2, 1024, 20.0, 1.0, (1.2,)))) as sim:
         assert sim.kernel == gpu_capi.CE_KERNEL_GENERIC
 
 
