@@ -370,42 +370,51 @@ template cudaError_t launch_step_generic<double>(const StepArgs<double>&, int, c
 //   a'(t_n) = a'_{n+1/2} - dt/2 a''_n;  u = v(t_n) - (a'(t_n)/a_n) f
 // With raw_u (start-up input) u is w itself.
 
-template <typename T, int NF, int DIMS>
+// Per-site quantities in the compute type C: f, u(t_n), the forward-difference
+// gradient term sum_d (f(x+e_d) - f(x))^2 and V(f).  The sums (k_diag) use C =
+// the storage type, with per-thread partials in C folded into FP64 every 16
+// sites as in the step kernels: for FP32 storage the inputs carry 2^-24
+// relative rounding already, and FP64 per-site arithmetic (one conversion per
+// neighbour load) made the pass bound by GB300's FP64 rate.  The synchronised
+// velocity download (k_sync_u_range) keeps C = double.
+template <typename T, typename C, int NF, int DIMS>
 __device__ __forceinline__ void site_u(const DiagArgs<T>& p, int64_t s, const SiteWalk<DIMS>& at,
-                                       double (&fv)[NF], double (&u)[NF], double (&g2)[NF]) {
+                                       C (&fv)[NF], C (&u)[NF], C (&g2)[NF], C& vsite) {
   int64_t nb[2 * DIMS];
   neighbours<DIMS>(s, at, p.N, nb);
-  double lap[NF];
+  C lap[NF];
+  const C idx2 = (C)p.inv_dx2;
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     const T* fi = p.f[i];
-    fv[i] = (double)fi[s];
-    double acc = 0.0, gg = 0.0;
+    fv[i] = (C)fi[s];
+    C acc = C(0), gg = C(0);
 #pragma unroll
     for (int d = 0; d < DIMS; ++d) {
-      const double fp = (double)fi[nb[2 * d]], fm = (double)fi[nb[2 * d + 1]];
-      acc += (fp + fm) - 2.0 * fv[i];
+      const C fp = (C)fi[nb[2 * d]], fm = (C)fi[nb[2 * d + 1]];
+      acc += (fp + fm) - C(2) * fv[i];
       gg += (fp - fv[i]) * (fp - fv[i]);
     }
-    lap[i] = acc * p.inv_dx2;
+    lap[i] = acc * idx2;
     g2[i] = gg;
   }
+  C dv[NF];
+  C q[3] = {(C)p.q[0], (C)p.q[1], (C)p.q[2]};
+  model_dv<C, NF>(fv, q, dv, vsite);
   if (p.raw_u) {
 #pragma unroll
-    for (int i = 0; i < NF; ++i) u[i] = (double)p.w[i][s];
+    for (int i = 0; i < NF; ++i) u[i] = (C)p.w[i][s];
     return;
   }
   const DevScalars sc = *p.sc;
-  double dv[NF], vs;
-  double q[3] = {p.q[0], p.q[1], p.q[2]};
-  model_dv<double, NF>(fv, q, dv, vs);
-  const double h = p.expansion ? (sc.ap - 0.5 * p.dt * sc.app) / sc.a : 0.0;
-  const double sterm = p.expansion ? sc.s : 0.0;
+  const C h = p.expansion ? (C)((sc.ap - 0.5 * p.dt * sc.app) / sc.a) : C(0);
+  const C sterm = p.expansion ? (C)sc.s : C(0);
+  const C half_dt = (C)(0.5 * p.dt);
   const T cT = (T)sc.c;
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     const T vh = fmaT(cT, p.f[i][s], p.w[i][s]);
-    const double vsync = (double)vh - 0.5 * p.dt * (lap[i] - dv[i] + sterm * fv[i]);
+    const C vsync = (C)vh - half_dt * (lap[i] - dv[i] + sterm * fv[i]);
     u[i] = vsync - h * fv[i];
   }
 }
@@ -415,31 +424,43 @@ template <typename T, int NF, int DIMS>
 __global__ void __launch_bounds__(256) k_diag(const DiagArgs<T> p) {
   constexpr int NV = 4 * NF + 1;
   double acc[NV];
+  T part[NV];   // per-thread partials in the storage type, folded into acc every 16 sites
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  double shift[NF];
+  for (int k = 0; k < NV; ++k) {
+    acc[k] = 0.0;
+    part[k] = T(0);
+  }
+  T shift[NF];
 #pragma unroll
-  for (int i = 0; i < NF; ++i) shift[i] = (double)p.f[i][0];
+  for (int i = 0; i < NF; ++i) shift[i] = p.f[i][0];
+  int since_flush = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   SiteWalk<DIMS> at;
   at.init(s0, stride, p.N);
   for (int64_t s = s0; s < p.S; s += stride, at.advance(p.N)) {
-    double fv[NF], u[NF], g2[NF];
-    site_u<T, NF, DIMS>(p, s, at, fv, u, g2);
-    double dv[NF], vs;
-    double q[3] = {p.q[0], p.q[1], p.q[2]};
-    model_dv<double, NF>(fv, q, dv, vs);
+    T fv[NF], u[NF], g2[NF], vs;
+    site_u<T, T, NF, DIMS>(p, s, at, fv, u, g2, vs);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
-      acc[i] += 0.5 * u[i] * u[i];
-      acc[NF + i] += g2[i];
-      const double df = fv[i] - shift[i];
-      acc[2 * NF + 1 + i] += df;
-      acc[3 * NF + 1 + i] += df * df;
+      part[i] += T(0.5) * u[i] * u[i];
+      part[NF + i] += g2[i];
+      const T df = fv[i] - shift[i];
+      part[2 * NF + 1 + i] += df;
+      part[3 * NF + 1 + i] += df * df;
     }
-    acc[2 * NF] += vs;
+    part[2 * NF] += vs;
+    if (++since_flush == 16) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        acc[k] += (double)part[k];
+        part[k] = T(0);
+      }
+      since_flush = 0;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] += (double)part[k];
   __shared__ double red[8][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -515,8 +536,8 @@ __global__ void __launch_bounds__(256) k_sync_u_range(const DiagArgs<T> p) {
   at.init(p.s0 + k0, stride, p.N);
   for (int64_t k = k0; k < p.count; k += stride, at.advance(p.N)) {
     const int64_t s = p.s0 + k;
-    double fv[NF], u[NF], g2[NF];
-    site_u<T, NF, DIMS>(p, s, at, fv, u, g2);
+    double fv[NF], u[NF], g2[NF], vs;
+    site_u<T, double, NF, DIMS>(p, s, at, fv, u, g2, vs);
 #pragma unroll
     for (int i = 0; i < NF; ++i) p.u_out[(int64_t)i * p.count + k] = u[i];
   }

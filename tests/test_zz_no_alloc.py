@@ -53,6 +53,11 @@ def test_noalloc_moments_match_handle_moments_twice(gpu_capi, precision):
     stream = torch.cuda.current_stream()
     code = capi.CE_F32 if precision == "f32" else capi.CE_F64
     scale = np.maximum(np.abs(ref_mean), np.sqrt(ref_var))
+    # The handle's pass keeps per-thread partials in the storage type over 16 sites
+    # before FP64: in FP32 each partial carries up to 16 x 2^-24 of its largest term
+    # (|f - f(0)| up to a few standard deviations), so ~1e-5 of the spread; in FP64
+    # the two paths agree to rounding.
+    tol_m, tol_v = (1e-12, 1e-6) if precision == "f64" else (1e-5, 1e-5)
     for _ in range(2):
         out_mean.fill_(float("nan"))
         out_var.fill_(float("nan"))
@@ -61,5 +66,5 @@ def test_noalloc_moments_match_handle_moments_twice(gpu_capi, precision):
         torch.cuda.synchronize()
         mean = out_mean.cpu().numpy()
         var = out_var.cpu().numpy()
-        assert np.all(np.abs(mean - ref_mean) <= 1e-12 * scale + 1e-15), (mean, ref_mean)
-        np.testing.assert_allclose(var, ref_var, rtol=1e-6, atol=1e-18)
+        assert np.all(np.abs(mean - ref_mean) <= tol_m * scale + 1e-15), (mean, ref_mean)
+        np.testing.assert_allclose(var, ref_var, rtol=tol_v, atol=1e-18)
