@@ -147,6 +147,40 @@ def test_fp32_storage_error_against_fp64_oracle(gpu_capi, orc):
         np.testing.assert_allclose(var, vref, rtol=1e-3)
 
 
+def test_plain_fp64_case_over_its_full_1000_steps(gpu_capi, orc):
+    """The plain method in FP64 (3D 32^3, 2 fields, q = 1.2, L = 20, dt = 0.05, no
+    expansion, amplitude 1e-4) for the full 1000 steps against the oracle: fields,
+    velocities and the energy."""
+    dims, N, L, dt, nf, q = 3, 32, 20.0, 0.05, 2, (1.2,)
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, False, 1000)
+    with sim:
+        assert per_field_err(f, ref.f, nf) <= 1e-10
+        assert per_field_err(v, ref.v, nf) <= 1e-10
+        assert sc.step == 1000 and sc.a == 1.0
+        en, en_ref = sim.energy(), orc.energy(ref)
+        assert en["E"] == pytest.approx(en_ref["E"], rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_long_nonlinear_run_statistics_against_oracle(gpu_capi, orc, precision):
+    """A long run in the nonlinear regime (3D 32^3, 2 fields, expansion on,
+    amplitude 1e-2, 2000 steps): where the evolution is chaotic, runs are compared
+    through means, variances, total energy and a(t), each within 1e-3."""
+    dims, N, L, dt, nf, q = 3, 32, 20.0, 0.05, 2, (1.2,)
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, dims, N, L, dt, nf, q, True, 2000, precision=precision,
+                                  amp=1e-2)
+    with sim:
+        assert sc.step == 2000
+        assert abs(sc.a - ref.scale.a) <= 1e-3 * ref.scale.a
+        en, en_ref = sim.energy(), orc.energy(ref)
+        assert en["E"] == pytest.approx(en_ref["E"], rel=1e-3)
+        mean, var = sim.means_variances()
+        mref, vref = orc.means_variances(ref.p, ref.f)
+        scale = np.maximum(np.abs(mref), np.sqrt(vref))
+        assert np.all(np.abs(mean - mref) <= 1e-3 * scale), (mean, mref)
+        np.testing.assert_allclose(var, vref, rtol=1e-3)
+
+
 def test_nonfinite_state_is_reported_not_faulted(gpu_capi):
     """A state whose potential overflows makes the global sums non-finite: the
     device latches CE_ENONFINITE and the next synchronising call returns it."""
