@@ -6,8 +6,9 @@
   and its 1D, 2D and 3D parts alone, one ``k_step_batched`` launch per step;
 * ``batch_3d``: homogeneous batches of about 100 M sites of one 3D side;
 * ``single``: one lattice stepped by ``ce_step`` with the generic kernel and
-  with the row kernel (``CE_KERNEL_ROWS``, the automatic choice for 2D sides
-  >= 512 and 3D sides >= 64 (FP32) / 256 (FP64) outside the z-sweep kernel).
+  with the row kernel (``CE_KERNEL_ROWS``, the automatic FP32 choice for 2D
+  sides >= 512 and 3D sides >= 64 outside the z-sweep kernel; in FP64 the
+  automatic choice is the generic kernel, which runs two passes in 2D/3D).
 
 Times are CUDA events on the library's stream around ``steps`` steps after
 ``warmup`` steps (graphs of 32 launches); ``frac`` is the algorithmic 16 B per
