@@ -41,12 +41,13 @@
 
 #include "ce_device.cuh"
 #include "ce_internal.h"
+#include "ce_plan.h"
 #include "ce_tma.cuh"
 
 namespace ce {
 namespace {
 
-constexpr int kWarps = 8;
+constexpr int kWarps = plan::kRowWarps;   // 8 (the launch models in ce_plan.h assume it)
 constexpr int kThreads = 32 * kWarps;
 // Tensor-map box shapes of a 3D member, per (buffer parity, field, f or w):
 // row boxes one segment wide and rows + 2, rows + 1, 1, nlast + 1 and nlast
@@ -620,35 +621,6 @@ cudaError_t batch_prepare(int prec, int nf, int* per_sm) {
   return prec == CE_F32 ? prepare_t<float>(nf, per_sm) : prepare_t<double>(nf, per_sm);
 }
 
-// Lanes per 3D row segment, as log2: the segment width (32, 16 or 8 lanes x VX
-// sites) that pads a row of N sites least, the widest on a tie.  Depends on N
-// only, so a lattice's items do not depend on the rest of the batch.
-int seg_log2_for(int N, int VX) {
-  int best = 5;
-  int64_t best_pad = INT64_MAX;
-  for (int sl = 5; sl >= 3; --sl) {
-    const int64_t W = (int64_t)VX << sl;
-    const int64_t pad = (N + W - 1) / W * W;
-    if (pad < best_pad) {
-      best_pad = pad;
-      best = sl;
-    }
-  }
-  return best;
-}
-
-// Items build_tables cuts a lattice into (same loops, counted).
-int64_t item_count(int dims, int64_t N, int VX, int sweep_len) {
-  const int64_t L = std::max<int64_t>(1, std::min<int64_t>(sweep_len, N));
-  const int64_t span = ce::kWarps * 32 * VX;
-  if (dims == 3) {
-    const int sl = seg_log2_for((int)N, VX);
-    const int64_t W = (int64_t)VX << sl, rows = (int64_t)ce::kWarps << (5 - sl);
-    return ((N + W - 1) / W) * ((N + rows - 1) / rows) * ((N + L - 1) / L);
-  }
-  if (dims == 2) return ((N + span - 1) / span) * ((N + L - 1) / L);
-  return (N + span - 1) / span;
-}
 
 // Cut every member into items of about kWarps x 32 x VX x sweep_len sites.
 template <typename T>
@@ -668,7 +640,7 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
       per[k].push_back({ce::BItem{(int)k, x0, y0, s0, s1}, cost});
     };
     if (s->dims == 3) {
-      const int sl = seg_log2_for(N, VX);
+      const int sl = ce::plan::seg_log2_for(N, VX);
       const int W = VX << sl, rows = ce::kWarps << (5 - sl);
       // x-neighbouring items next to each other in the queue, then y: items that
       // share halo rows and halo sectors start together and read them from L2
@@ -706,7 +678,7 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
     m.done = b->d_done + k;
     m.dims = s->dims;
     m.N = (int)s->N;
-    m.seg_log2 = s->dims == 3 ? seg_log2_for((int)s->N, VX) : 5;
+    m.seg_log2 = s->dims == 3 ? ce::plan::seg_log2_for((int)s->N, VX) : 5;
     m.p0 = s->cur ^ b->par;
     m.first_item = (int)items.size();
     m.n_items = (int)per[k].size();
@@ -754,7 +726,7 @@ int encode_maps(ce_batch* b, std::vector<ce::BMember<T>>& mem) {
     if (s->dims != 3) continue;
     first[k] = at;
     const int64_t N = s->N;
-    const int sl = seg_log2_for((int)N, VX);
+    const int sl = ce::plan::seg_log2_for((int)N, VX);
     const cuuint32_t W = (cuuint32_t)(VX << sl), rows = (cuuint32_t)(ce::kWarps << (5 - sl));
     const cuuint32_t groups = (cuuint32_t)((N + rows - 1) / rows);
     const cuuint32_t nlast = (cuuint32_t)(N - (int64_t)rows * (groups - 1));
@@ -852,65 +824,6 @@ void advance_members(ce_batch* b, int64_t steps) {
 
 cudaError_t ce::batch_wait(ce_batch* b) { return b ? cudaStreamSynchronize(b->stream) : cudaSuccess; }
 
-namespace {
-
-// Predicted duration, in plane-times, of one launch on a lattice alone cut into
-// items of L planes along the sweep axis (plus two halo planes and a start-up
-// cost of about two planes each), taken from the queue in build order by
-// `slots` resident CTAs.  The active CTAs share HBM equally and one CTA streams
-// at most 1.25x its share under full load: a processor-sharing model whose two
-// constants were chosen on timings of single 2D and 3D lattices (a lattice of
-// few columns needs short items to keep the CTAs busy, a large one long items
-// to amortise the halo planes, and a fraction of a wave costs a whole item).
-double rows_predicted_time(int dims, int64_t N, int VX, int L, int slots) {
-  const int64_t Lc = std::max<int64_t>(1, std::min<int64_t>(L, N));
-  const int64_t nz = (N + Lc - 1) / Lc, last = N - (nz - 1) * Lc;
-  const int64_t cols = item_count(dims, N, VX, (int)N);   // items of one full-length chunk
-  const int64_t n = cols * nz;
-  // 3D items run z-chunk by z-chunk (the short last chunk at the end), 2D items column by column
-  auto planes = [&](int64_t k) -> double {
-    const bool tail = dims == 3 ? k >= cols * (nz - 1) : (k % nz) == nz - 1;
-    return (double)((tail ? last : Lc) + 2 + 2);
-  };
-  constexpr double kSoloSpeedup = 1.25;
-  std::vector<double> rem;
-  rem.reserve(slots);
-  int64_t next = 0;
-  while (next < n && (int)rem.size() < slots) rem.push_back(planes(next++));
-  double t = 0.0;
-  while (!rem.empty()) {
-    const double rate = std::min(kSoloSpeedup, (double)slots / (double)rem.size());
-    const double m = *std::min_element(rem.begin(), rem.end());
-    t += m / rate;
-    size_t keep = 0;
-    for (size_t i = 0; i < rem.size(); ++i)
-      if (rem[i] - m > 1e-9) rem[keep++] = rem[i] - m;
-    size_t freed = rem.size() - keep;
-    rem.resize(keep);
-    for (; freed > 0 && next < n; --freed) rem.push_back(planes(next++));
-  }
-  return t;
-}
-
-// Item length of a lattice alone: the candidate with the least predicted time
-// (ties to the longer item).  1D lattices are one row; their items do not depend on it.
-int rows_item_length(int dims, int64_t N, int VX, int slots) {
-  static const int kCand[] = {128, 96, 64, 48, 32, 24, 16, 12, 8, 4};
-  if (dims == 1) return 128;
-  int best = 128;
-  double best_t = -1.0;
-  for (int L : kCand) {
-    if (L > N && L != 128) continue;
-    const double t = rows_predicted_time(dims, N, VX, L, slots);
-    if (best_t < 0.0 || t < best_t * (1.0 - 1e-3)) {
-      best_t = t;
-      best = L;
-    }
-  }
-  return best;
-}
-
-}  // namespace
 
 // A private one-lattice batch that lets ce_step run the batched kernel on a
 // single handle (lattices the z-sweep kernel does not cover).  It works on the
@@ -945,7 +858,7 @@ int ce::rows_create(ce_sim* s, ce_batch** out) {
     delete b;
     return bcuda(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "ce_create: row-kernel occupancy");
   }
-  b->sweep_len = rows_item_length(s->dims, s->N, 16 / s->esize, per_sm * sms);
+  b->sweep_len = ce::plan::rows_item_length(s->dims, s->N, 16 / s->esize, per_sm * sms);
   const int cur = s->cur;
   s->cur = 0;   // member parity 0: the launch's parity argument is the input buffer set
   int rc = b->prec == CE_F32 ? upload_tables<float>(b) : upload_tables<double>(b);

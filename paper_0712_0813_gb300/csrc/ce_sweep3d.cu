@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ce_internal.h"
+#include "ce_plan.h"
 #include "ce_sweep3d.cuh"
 
 namespace ce {
@@ -49,51 +50,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
-// Predicted duration (in plane-times of a CTA sharing its SM) of a launch of
-// cols x gz CTAs, each sweeping its chunk of N / gz planes plus 2 halo planes
-// and a start-up of about 4 planes.  Blocks are handed out in grid order to the
-// SM slots that free up; a CTA runs 1.32x faster while it is alone on its SM
-// (ncu: 2.2k against 2.9k cycles per plane at 256^3), and an SM never streams
-// faster than per_sm CTAs sharing it.  The lone-CTA speed-up is what makes a
-// partial wave cheaper than a whole one: at 256^3 the model prefers 4 chunks
-// (0.84 of a wave; measured 93.3 us) to 14 (101.6 us), which a count of whole
-// waves would pick.  Event-driven: one heap entry per SM.
-double grid_time(int64_t N, int64_t cols, int gz, int per_sm, int sms) {
-  constexpr double kStart = 4.0, kSolo = 1.32;
-  const double cap = (double)per_sm;
-  auto rate = [&](size_t n) { return std::min(kSolo, cap / (double)n); };
-  const int64_t nblk = cols * gz;
-  auto work = [&](int64_t b) {
-    const int64_t zc = b / cols;
-    return (double)((zc + 1) * N / gz - zc * N / gz + 2) + kStart;
-  };
-  std::vector<std::vector<double>> rem(sms);
-  std::vector<double> last(sms, 0.0);
-  int64_t next = 0;
-  for (int r = 0; r < per_sm; ++r)
-    for (int s = 0; s < sms && next < nblk; ++s) rem[s].push_back(work(next++));
-  using Ev = std::pair<double, int>;
-  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> heap;
-  for (int s = 0; s < sms; ++s)
-    if (!rem[s].empty()) heap.push({*std::min_element(rem[s].begin(), rem[s].end()) / rate(rem[s].size()), s});
-  double end = 0.0;
-  while (!heap.empty()) {
-    const auto [t, s] = heap.top();
-    heap.pop();
-    const double done = (t - last[s]) * rate(rem[s].size());
-    size_t keep = 0, freed = 0;
-    for (double w : rem[s]) {
-      if (w - done > 1e-9) rem[s][keep++] = w - done;
-      else ++freed;
-    }
-    rem[s].resize(keep);
-    for (; freed > 0 && next < nblk; --freed) rem[s].push_back(work(next++));
-    last[s] = t;
-    end = std::max(end, t);
-    if (!rem[s].empty()) heap.push({t + *std::min_element(rem[s].begin(), rem[s].end()) / rate(rem[s].size()), s});
-  }
-  return end;
-}
 
 // Default variant when the caller gives no hint: the first that applies in
 // this order of preference.
@@ -154,24 +110,7 @@ cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2]
     if (zchunks_hint > N / 2) return cudaErrorInvalidConfiguration;
     plan.gz = zchunks_hint;
   } else {
-    // z-chunks: among chunks of at most 64 planes, the count with the least
-    // predicted launch time (grid_time).  Longer chunks measured slower on
-    // large lattices than the model says (640^3: 3 chunks 1363 us, 12 chunks
-    // 1279 us); with the cap the pick was the measured best, or within 1-5% of
-    // it, on every FP32 lattice timed (128^3 to 768^3, 8- and 16-row tiles).
-    constexpr int kMaxChunk = 64;
-    const int gz_min = (int)std::max<int64_t>(1, (N + kMaxChunk - 1) / kMaxChunk);
-    double best = 1e300;
-    int best_gz = (int)std::min<int64_t>(gz_min, N / 2);
-    for (int gz = gz_min; gz <= N / 4 && gz <= 128; ++gz) {
-      if (gz > gz_min && (int64_t)plan.gx * plan.gy * gz > 32LL * per_sm * sms) break;   // 32 waves: no tail left to win
-      const double t = grid_time(N, (int64_t)plan.gx * plan.gy, gz, per_sm, sms);
-      if (t < best * (1.0 - 1e-6)) {
-        best = t;
-        best_gz = gz;
-      }
-    }
-    plan.gz = best_gz;
+    plan.gz = plan::auto_zchunks(N, (int64_t)plan.gx * plan.gy, per_sm, sms);   // ce_plan.h
   }
 
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
