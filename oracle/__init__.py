@@ -17,6 +17,11 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   spectrum (numpy FFT + binning) pinned: Parseval, plane-wave and constant fields
   local.step_at (one step at chosen sites, numpy; ``oracle/local.py``) pinned:
                          bit-identical to orc_step on whole small lattices
+  local.drifted_sums (G and V of f + dt v, streamed over slabs) pinned: equal
+                         to orc_gradient_mean / orc_potential_mean to rounding
+  omp_init/omp_step (``clusterlat_oracle_omp.c``, the same loops with OpenMP
+                         threads; timing only) checked equal to orc_init /
+                         orc_step to rounding
   start-up conventions (a(0)=1, u-velocity, kappa default), the IC recipe and the
   Courant rule are conventions the paper leaves open: parity unpinned there.
 """
@@ -33,20 +38,29 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "clusterlat_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "clusterlat_oracle_omp.c")
+_OMP_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle_omp.so")
 _lib = None
+_omp_lib = None
+
+
+def _compile(src: str, out: str, extra: list, force: bool):
+    stale = (not os.path.exists(out)
+             or os.path.getmtime(out) < os.path.getmtime(src)
+             or os.path.getmtime(out) < os.path.getmtime(_SRC[:-2] + ".h"))
+    if force or stale:
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-Wall", *extra, "-o", tmp, src, "-lm"])
+        os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, no GPU)."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` and its OpenMP
+    timing copy into ``oracle/_build/liboracle_omp.so`` (gcc, no GPU)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC[:-2] + ".h"))
-    if force or stale:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-Wall", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    _compile(_SRC, _LIB_PATH, [], force)
+    _compile(_OMP_SRC, _OMP_LIB_PATH, ["-fopenmp"], force)
     return _LIB_PATH
 
 
@@ -188,6 +202,56 @@ def step(st: State, n: int) -> State:
                           ctypes.byref(st.scale), int(n))
     if rc != 0:
         raise RuntimeError(f"orc_step failed ({rc})")
+    return st
+
+
+def _load_omp():
+    """The OpenMP copy of the oracle's loops (``clusterlat_oracle_omp.c``), used
+    only to time the CPU baseline on all host cores."""
+    global _omp_lib
+    if _omp_lib is None:
+        build()
+        lib = ctypes.CDLL(_OMP_LIB_PATH)
+        P = ctypes.POINTER
+        pd = P(ctypes.c_double)
+        lib.orcp_threads.restype = ctypes.c_int
+        lib.orcp_threads.argtypes = []
+        lib.orcp_set_threads.restype = None
+        lib.orcp_set_threads.argtypes = [ctypes.c_int]
+        lib.orcp_init.restype = ctypes.c_int
+        lib.orcp_init.argtypes = [P(Model), pd, pd, P(Scale)]
+        lib.orcp_step.restype = ctypes.c_int
+        lib.orcp_step.argtypes = [P(Model), pd, pd, P(Scale), ctypes.c_longlong]
+        _omp_lib = lib
+    return _omp_lib
+
+
+def omp_threads(n: int | None = None) -> int:
+    """Set (n > 0) and return the number of OpenMP threads of the timing copy."""
+    lib = _load_omp()
+    if n:
+        lib.orcp_set_threads(int(n))
+    return lib.orcp_threads()
+
+
+def omp_init(p: Params, f0: np.ndarray, u0: np.ndarray) -> State:
+    """``init`` through the OpenMP timing copy (same result to rounding)."""
+    f = np.array(f0, dtype=np.float64).reshape(-1).copy()
+    v = np.array(u0, dtype=np.float64).reshape(-1).copy()
+    assert f.size == p.nf * p.S and v.size == f.size
+    sc = Scale()
+    rc = _load_omp().orcp_init(ctypes.byref(p.model()), _ptr(f), _ptr(v), ctypes.byref(sc))
+    if rc != 0:
+        raise RuntimeError(f"orcp_init failed ({rc})")
+    return State(p, f, v, sc)
+
+
+def omp_step(st: State, n: int) -> State:
+    """``step`` through the OpenMP timing copy (same result to rounding)."""
+    rc = _load_omp().orcp_step(ctypes.byref(st.p.model()), _ptr(st.f), _ptr(st.v),
+                               ctypes.byref(st.scale), int(n))
+    if rc != 0:
+        raise RuntimeError(f"orcp_step failed ({rc})")
     return st
 
 

@@ -127,3 +127,55 @@ def step_at(p, sites, stencil, f_st, v_st, a: float, ap: float, G: float, V: flo
     F = lap - dv + s * fs
     v1 = v_st[:, k0] + dt * F                             # kick
     return SampledStep(fs, v1, a1, ap1, app1)
+
+
+def drifted_sums(p, read, slab: int = 16):
+    """The step's global sums (row A5 of the step; reading c-4 for G): the mean
+    gradient energy G = (1/S) sum_x sum_i sum_d 1/2 ((g_i(x+e_d) - g_i(x))/dx)^2
+    and the mean potential V = (1/S) sum_x V(g(x)) of the drifted fields
+    g = f + dt v, over the whole lattice, without holding it in memory.
+
+    read(k0, k1) returns (f, v): float64 arrays of shape (nf, k1 - k0, *rest)
+    holding f(t) and v(t+dt/2) on the hyperplanes k0 .. k1-1 of the slowest
+    axis (z in 3D, y in 2D, x in 1D), x fastest.  Slabs of `slab` hyperplanes
+    are read in order, each with the next hyperplane (the first one again at
+    the end: the periodic wrap) for the forward difference along the slowest
+    axis; within a hyperplane the forward differences wrap with np.roll.  The
+    drift f + dt v is the same single rounding as orc_step's; the sums add in
+    a different order than orc_gradient_mean / orc_potential_mean (per slab,
+    then across slabs), so they agree with those to rounding.
+    Returns (G, V, G_per_field)."""
+    n = p.N
+    dx = p.L / p.N
+    q = list(p.q) + [0.0] * 3
+    G = np.zeros(p.nf)
+    Vsum = 0.0
+    first = None
+    for k0 in range(0, n, slab):
+        k1 = min(n, k0 + slab)
+        f, v = read(k0, min(n, k1 + 1))
+        g = np.asarray(f, dtype=np.float64) + p.dt * np.asarray(v, dtype=np.float64)
+        if k0 == 0:
+            first = g[:, :1].copy()
+        if k1 == n:
+            g = np.concatenate([g, first], axis=1)
+        m = k1 - k0
+        body = g[:, :m]
+        for i in range(p.nf):
+            acc = 0.0
+            # slowest axis: hyperplane k+1 minus hyperplane k
+            dz = (g[i, 1:m + 1] - body[i]) / dx
+            acc += float(np.sum(0.5 * dz * dz))
+            # the faster axes, periodic within each hyperplane
+            for ax in range(1, p.dims):
+                d = (np.roll(body[i], -1, axis=ax) - body[i]) / dx
+                acc += float(np.sum(0.5 * d * d))
+            G[i] += acc
+        phi = body[0]
+        pot = 0.25 * phi * phi * phi * phi
+        for i in range(1, p.nf):
+            pot = pot + 0.5 * q[i - 1] * phi * phi * body[i] * body[i]
+        Vsum += float(np.sum(pot))
+    S = float(p.N) ** p.dims
+    G = G / S
+    return float(np.sum(G)), Vsum / S, G

@@ -11,16 +11,19 @@ a hundred seconds per step there), so one GPU step is checked site by site:
 * the GPU takes one step, and the new state is sampled at the sites;
 * the oracle's per-site restatement of one step (`oracle/local.py`, pinned
   equal to `orc_step` on whole lattices) computes the new state from the first
-  sample.  The step's global sums G and V enter only the scale factor; the
-  oracle takes them from `ce_energy` (the separate diagnostic kernel's FP64 sums
-  of the stored fields), so the scale factor the fused step kernel computed from
-  its own FP32 partial sums is checked against them too.
+  sample.  The step's global sums G and V (they enter only the scale factor)
+  come from the oracle too: `local.drifted_sums` (pinned equal to the C
+  oracle's sums) streams the whole lattice's state before the step, a slab of
+  z-planes at a time, and sums the gradient and potential energy of the
+  drifted fields f + dt v in FP64.  No oracle input comes from a GPU output
+  other than the sampled state being checked.
 
 Workloads and launch plans are the ones the benchmark times: 3D 256^3, 2
 fields, dt = 0.02 (plan 8 rows / 4 stages / 4 z-chunks); 3D 512^3, 4 fields,
-q = (0.8, 5, 40) (plan 8 / 5 / 8); 3D 1024^3, 2 fields (plan 16 / 4 / 8); all
-FP32 storage with expansion; and the 96-lattice mixed batch (FP32, batched
-kernel, the item length the bench's autotuner picks).  Tolerances: f and v
+q = (0.8, 5, 40) (plan 8 / 5 / 8); 3D 1024^3, 2 fields (the automatic plan,
+then 16 / 4 / 8 on the same state); all FP32 storage with expansion; and the
+96-lattice mixed batch (FP32, batched kernel, the item length the bench's
+autotuner picks).  Tolerances: f and v
 within an error bound of one FP32 step derived from the arithmetic
 (`check_one_step`; on the finest lattices the Laplacian's 1/dx^2 weights make
 the FP32 rounding of g the dominant term), a(t) to 1e-12, and a', a'' to 1e-5
@@ -62,41 +65,62 @@ def plan_sites(N, tx, ty, zchunks, n_random=3000, seed=11):
     return np.unique(np.concatenate([edges, rand]).astype(np.int64))
 
 
+def oracle_sums(local, p, sim):
+    """G and V of the drifted fields f + dt v over the whole lattice, computed
+    by the oracle (`local.drifted_sums`) from the lattice's current staggered
+    state, read a slab of hyperplanes of the slowest axis (about 16 M sites)
+    at a time."""
+    plane = p.N ** (p.dims - 1)
+    slab = max(1, (1 << 24) // plane)
+    rest = (p.N,) * (p.dims - 1)
+
+    def read(k0, k1):
+        f, v, _ = sim.sample_fields(np.arange(k0 * plane, k1 * plane, dtype=np.int64))
+        return f.reshape((p.nf, k1 - k0) + rest), v.reshape((p.nf, k1 - k0) + rest)
+
+    G, V, _ = local.drifted_sums(p, read, slab=max(1, min(slab, p.N)))
+    return G, V
+
+
 SINGLE = [
-    # name, N, nf, q, dt (None: Courant rule), plan (rows, stages, zchunks)
-    ("256cube", 256, 2, (1.2,), 0.02, (8, 4, 4)),
-    ("512cube_4field", 512, 4, (0.8, 5.0, 40.0), None, (8, 5, 8)),
-    ("1024cube", 1024, 2, (1.2,), None, (16, 4, 8)),
+    # name, N, nf, q, dt (None: Courant rule), plans (rows, stages, zchunks; 0 = automatic)
+    ("256cube", 256, 2, (1.2,), 0.02, [(8, 4, 4)]),
+    ("512cube_4field", 512, 4, (0.8, 5.0, 40.0), None, [(8, 5, 8)]),
+    ("1024cube", 1024, 2, (1.2,), None, [(0, 0, 0), (16, 4, 8)]),
 ]
 
 
-@pytest.mark.parametrize("name,N,nf,q,dt,plan", SINGLE, ids=[c[0] for c in SINGLE])
-def test_full_size_sampled_step(gpu_capi, orc, name, N, nf, q, dt, plan):
+@pytest.mark.parametrize("name,N,nf,q,dt,plans", SINGLE, ids=[c[0] for c in SINGLE])
+def test_full_size_sampled_step(gpu_capi, orc, name, N, nf, q, dt, plans):
     import torch
     from oracle import local
     capi = gpu_capi
     L = 20.0
     if dt is None:
         dt = courant_dt(3, N, L, 1.0, q)
+    p = orc.Params(dims=3, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
     f0, u0 = lattice_ics(3, N, L, nf, q=q, seed=1, backend="torch" if N >= 512 else "numpy")
     torch.cuda.empty_cache()
-    rows, stages, zchunks = plan
+    rows, stages, zchunks = plans[0]
     with capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision="f32",
                          kernel="sweep", tile_rows=rows, stages=stages, zchunks=zchunks) as sim:
-        assert sim.sweep_plan == plan
         sim.set_fields(f0, u0)
         del f0, u0
         gc.collect()
         sim.step(3)
-        sites = plan_sites(N, 128, rows, zchunks)
-        stencil = local.stencil_sites(3, N, sites)
-        before = sim.sample_fields(stencil)
-        sim.step(1)
-        after = sim.sample_fields(sites)
-        en = sim.energy()
-    p = orc.Params(dims=3, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
-    check_one_step(orc, local, p, before, after, sites, stencil, float(np.sum(en["G"])), en["V"])
-    assert after[2].step == 4
+        for k, plan in enumerate(plans):
+            if k:
+                sim.replan(*plan)
+            used = sim.sweep_plan
+            assert all(want in (0, got) for want, got in zip(plan, used))
+            sites = plan_sites(N, 128, used[0], used[2])
+            stencil = local.stencil_sites(3, N, sites)
+            before = sim.sample_fields(stencil)
+            G, V = oracle_sums(local, p, sim)
+            sim.step(1)
+            after = sim.sample_fields(sites)
+            check_one_step(orc, local, p, before, after, sites, stencil, G, V)
+            assert after[2].step == 4 + k
 
 
 def test_mixed_batch_sampled_step(gpu_capi, orc):
@@ -115,7 +139,7 @@ def test_mixed_batch_sampled_step(gpu_capi, orc):
     stream = torch.cuda.Stream()
     tune = autotune.autotune_batch(sims, stream=stream, steps=4, warmup=1)
     rng = np.random.default_rng(17)
-    picks, befores = [], []
+    picks, befores, sums = [], [], []
     with capi.Batch(sims, sweep_len=tune["sweep_len"], stream=stream.cuda_stream) as b:
         b.step(2)
         b.synchronize()
@@ -127,12 +151,14 @@ def test_mixed_batch_sampled_step(gpu_capi, orc):
             stencil = local.stencil_sites(sp["dims"], sp["N"], sites)
             picks.append((sites, stencil))
             befores.append(s.sample_fields(stencil))
+            p = orc.Params(dims=sp["dims"], N=sp["N"], L=sp["L"], dt=sp["dt"], nf=sp["nf"], q=sp["q"],
+                           expansion=sp["expansion"])
+            sums.append(oracle_sums(local, p, s))
         b.step(1)
         b.synchronize()
-    for sp, s, (sites, stencil), before in zip(specs, sims, picks, befores):
+    for sp, s, (sites, stencil), before, (G, V) in zip(specs, sims, picks, befores, sums):
         after = s.sample_fields(sites)
-        en = s.energy()
         p = orc.Params(dims=sp["dims"], N=sp["N"], L=sp["L"], dt=sp["dt"], nf=sp["nf"], q=sp["q"],
                        expansion=sp["expansion"])
-        check_one_step(orc, local, p, before, after, sites, stencil, float(np.sum(en["G"])), en["V"])
+        check_one_step(orc, local, p, before, after, sites, stencil, G, V)
         s.close()

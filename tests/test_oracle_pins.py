@@ -406,3 +406,77 @@ def test_local_step_equals_orc_step(orc, dims, N, nf, q, expansion, dt):
     assert np.array_equal(part.f, res.f[:, some]) and np.array_equal(part.v, res.v[:, some])
     with pytest.raises(ValueError):
         local.step_at(p, some, some, fb[:, some], vb[:, some], a, ap, G, V)   # neighbours missing
+
+
+# ------------------------------------------- slab-streamed sums of the drift
+
+SUM_CASES = [(1, 64, 2, 7), (2, 3, 1, 2), (2, 20, 4, 6), (3, 3, 2, 1), (3, 17, 3, 5), (3, 32, 2, 16)]
+
+
+def _slab_reader(f, v, nf, dims, N):
+    sh = (nf,) + (N,) * dims
+    F, V = f.reshape(sh), v.reshape(sh)
+    return lambda k0, k1: (F[:, k0:k1], V[:, k0:k1])
+
+
+@pytest.mark.parametrize("dims,N,nf,slab", SUM_CASES)
+def test_drifted_sums_equal_whole_lattice_sums(orc, dims, N, nf, slab):
+    """local.drifted_sums, read slab by slab (slab sizes that leave a ragged
+    last slab, N = 3 where every neighbour wraps), gives the G and V that
+    orc_gradient_mean / orc_potential_mean give for the whole drifted array
+    f + dt v, to rounding (the two add in different orders)."""
+    from oracle import local
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    q = (1.2, 5.0, 40.0)[:max(nf - 1, 1)]
+    p = orc.Params(dims=dims, N=N, L=20.0, dt=0.03, nf=nf, q=q, expansion=True)
+    f, _ = lattice_ics(dims, N, 20.0, nf, q=q, seed=3, amp=1e-2)
+    v = np.random.default_rng(1).normal(size=f.shape)
+    G, V, Gp = local.drifted_sums(p, _slab_reader(f, v, nf, dims, N), slab=slab)
+    g = (f + p.dt * v).reshape(-1)
+    G0, Gp0 = orc.gradient_mean(p, g)
+    V0 = orc.potential_mean(p, g)
+    assert abs(G - G0) <= 1e-13 * G0
+    assert abs(V - V0) <= 1e-13 * V0
+    np.testing.assert_allclose(Gp, Gp0, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("dims,N,n", [(1, 24, (5,)), (2, 16, (3, 2)), (3, 12, (1, 4, 2))])
+def test_drifted_sums_plane_wave_closed_form(orc, dims, N, n):
+    """A plane wave A cos(k.x + theta) as the drifted field (v = 0) has mean
+    forward-difference gradient energy A^2 sum_d sin^2(k_d dx/2) / dx^2, and a
+    constant phi = c has V = c^4 / 4 (chi = 0)."""
+    from oracle import local
+    L, A = 7.0, 0.3
+    dx = L / N
+    p = orc.Params(dims=dims, N=N, L=L, dt=0.01, nf=2, q=(1.2,))
+    X = coords(dims, N, L)
+    k = [2 * math.pi * nd / L for nd in n]
+    chi = A * np.cos(sum(kd * Xd for kd, Xd in zip(k, X)) + 0.4).reshape(-1)
+    c = 0.7
+    f = np.stack([np.full(N ** dims, c), chi])
+    G, V, Gp = local.drifted_sums(p, _slab_reader(f, np.zeros_like(f), 2, dims, N), slab=5)
+    expect = A * A * sum(math.sin(kd * dx / 2) ** 2 for kd in k) / dx ** 2
+    assert abs(Gp[0]) == 0.0
+    assert abs(Gp[1] - expect) <= 1e-13 * expect
+    # V = c^4/4 + (q/2) c^2 <chi^2>, <chi^2> = A^2/2
+    assert abs(V - (c ** 4 / 4 + 0.6 * c * c * A * A / 2)) <= 1e-14
+
+
+# ------------------------------------------ OpenMP timing copy of the oracle
+
+def test_omp_copy_matches_serial_oracle(orc):
+    """The OpenMP copy of the oracle's loops (timed as the CPU baseline on all
+    host cores) reproduces the serial oracle on the expanding 32^3 lattice to
+    rounding: only the order of the global sums differs."""
+    from paper_0712_0813_gb300.icgen import lattice_ics
+    p = orc.Params(dims=3, N=32, L=20.0, dt=0.05, nf=2, q=(1.2,), expansion=True)
+    f0, u0 = lattice_ics(3, 32, 20.0, 2, q=(1.2,), seed=1, amp=1e-2)
+    orc.omp_threads(4)
+    assert orc.omp_threads() == 4
+    ser = orc.step(orc.init(p, f0, u0), 20)
+    par = orc.omp_step(orc.omp_init(p, f0, u0), 20)
+    assert np.abs(par.f - ser.f).max() <= 1e-13 * np.abs(ser.f).max()
+    assert np.abs(par.v - ser.v).max() <= 1e-12 * np.abs(ser.v).max()
+    assert abs(par.scale.a - ser.scale.a) <= 1e-14 * ser.scale.a
+    assert abs(par.scale.ap - ser.scale.ap) <= 1e-13 * abs(ser.scale.ap)
+    assert par.scale.step == ser.scale.step == 20
