@@ -149,7 +149,9 @@ typedef struct ce_sim ce_sim;
  * CE_ECUDA (no device / CUDA failure). */
 int ce_create(const ce_config* cfg, ce_sim** out);
 
-/* Load a state.  f, v: host float64, nf * N^dims each, layout above.
+/* Load a state (Sec. II: the program starts from initial conditions set on
+ * the lattice; Sec. III: f at integer time, v half a step later).  f, v: host
+ * float64, nf * N^dims each, layout above.
  *  mode CE_VEL_SYNC:      v = u(0); runs the start-up (a=1, a'(0) from the
  *                         Friedmann equation, half kick); sc must be NULL.
  *  mode CE_VEL_STAGGERED: f = f(t), v = f'(t+dt/2) and *sc the matching scalars;
@@ -169,17 +171,26 @@ int ce_step(ce_sim* sim, int64_t n);
 int ce_synchronize(ce_sim* sim);
 
 /* Per-field mean <f_i> and population variance <(f_i - <f_i>)^2> at the
- * current integer time, FP64 sums.  mean, var: host arrays of nf doubles.
- * Synchronises. */
+ * current integer time, FP64 sums.  Sec. II leaves the choice of outputs to
+ * the run's parameters; per-field means and population variances are the
+ * library's reading of the basic field statistics such a run writes out.
+ * mean, var: host arrays of nf doubles, owned by the caller.  Synchronises.
+ * Errors: CE_EINVAL (NULL argument), CE_ESTATE (no fields set), a latched
+ * device error, CE_ECUDA. */
 int ce_means_variances(ce_sim* sim, double* mean, double* var);
 
-/* Energies and scale factor at the current integer time.  Synchronises. */
+/* Energies and scale factor at the current integer time (Sec. II outputs;
+ * Abstract: evolution with expansion of the universe).  *out: caller-owned.
+ * Synchronises.  Errors: CE_EINVAL, CE_ESTATE, a latched device error, CE_ECUDA. */
 int ce_energy(ce_sim* sim, ce_energy_t* out);
 
-/* Copy the state out.  f, v: host float64 arrays of nf * N^dims.
+/* Copy the state out (Sec. II: the program writes field values on the
+ * lattice; Sec. III staggering of f and v).  f, v: caller-owned host float64
+ * arrays of nf * N^dims, layout above.
  *  mode CE_VEL_SYNC:      v = u(t) (synchronised); sc may be NULL.
  *  mode CE_VEL_STAGGERED: v = f'(t+dt/2); *sc (required) receives the scalars.
- * Synchronises. */
+ * Synchronises.  Errors: CE_EINVAL (NULL argument, or sc NULL with
+ * CE_VEL_STAGGERED), CE_ESTATE (no fields set), CE_ECUDA. */
 int ce_get_fields(ce_sim* sim, double* f, double* v, int mode, ce_scalars_t* sc);
 
 /* The staggered state at n chosen sites, without downloading the lattice (for
@@ -192,10 +203,15 @@ int ce_get_fields(ce_sim* sim, double* f, double* v, int mode, ce_scalars_t* sc)
  * fields set), a latched device error, CE_ECUDA. */
 int ce_sample_fields(ce_sim* sim, const int64_t* sites, int64_t n, double* f, double* v, ce_scalars_t* sc);
 
-/* Release the handle and its device memory.  NULL-safe. */
+/* Release the handle and its device memory (the end of a run, Sec. II).  Waits
+ * for the handle's queued work; a member of a batch leaves the batch unusable.
+ * NULL-safe; the handle must not be used afterwards. */
 void ce_free(ce_sim* sim);
 
-/* Thread-local description of the last error ("" if none). */
+/* Thread-local description of the last error ("" if none); the string is
+ * owned by the library and valid until the next call on this thread.  The
+ * paper has no counterpart (its program is run from the command line, Sec. II);
+ * this is how the library reports a failed call. */
 const char* ce_last_error(void);
 
 /* Bytes of device memory the handle holds (state + scratch). */
@@ -295,7 +311,10 @@ int ce_version(void);
  * GPU that loads it until the process exits; the call makes no cudaMalloc,
  * cudaFree or other allocating call.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress): make that first call
- * before any stream capture.  All calls share the array, so calls that overlap
+ * before any stream capture.  The address is cached per process and per device
+ * index for the life of the process: do not call this entry point again after
+ * cudaDeviceReset (or anything else that destroys the device's primary
+ * context) in the same process.  All calls share the array, so calls that overlap
  * on the GPU (other streams, other threads) race and must be serialised by the
  * caller; each call overwrites every scratch value it reads, so nothing needs
  * clearing between calls.

@@ -209,7 +209,7 @@ ce::DiagArgs<T> make_diag_args(const ce_sim* s, int raw_u) {
 
 int diag_blocks(const ce_sim* s) {
   int64_t want = (s->S + 255) / 256;
-  return (int)(want < ce::kDiagBlocksMax ? want : ce::kDiagBlocksMax);
+  return (int)(want < s->diag_blocks_max ? want : s->diag_blocks_max);
 }
 
 cudaError_t run_diag(const ce_sim* s, int raw_u) {
@@ -338,8 +338,10 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   else if (sweep_ok && (cfg->precision == CE_F32 || sweep_hinted || cfg->kernel == CE_KERNEL_SWEEP))
     s->kernel = CE_KERNEL_SWEEP;
   else s->kernel = rows_auto ? CE_KERNEL_ROWS : CE_KERNEL_GENERIC;
-  s->generic_blocks = ce::generic_blocks(S);
   cudaGetDevice(&s->device);
+  s->sms = ce::sm_count(s->device);
+  s->generic_blocks = ce::generic_blocks(S, s->sms);
+  s->diag_blocks_max = 8 * s->sms;
   if (cfg->stream) {
     s->stream = static_cast<cudaStream_t>(cfg->stream);
   } else {
@@ -378,7 +380,7 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
     sweep_blocks = std::max<int64_t>((int64_t)s->plan.gx * s->plan.gy * s->plan.gz, (s->N / tx) * (s->N / 4) * (s->N / 2));
   }
   int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, sweep_blocks), 1);
-  int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)ce::kDiagBlocksMax * 17);
+  int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)s->diag_blocks_max * 17);
   s->partials = static_cast<double*>(dalloc(s, (size_t)plen * 8));
   s->aux = static_cast<ce::DevAux*>(dalloc(s, sizeof(ce::DevAux)));
   s->chunk = std::min<int64_t>(S, kStagingChunk);

@@ -15,6 +15,7 @@
 // factor.  f is ping-ponged because neighbours of the old f are still being read
 // while the new one is written; the velocity state is ping-ponged for the same
 // reason (its neighbours are read to form g there).
+#include <atomic>
 #include <cstdint>
 
 #include "ce_device.cuh"
@@ -22,10 +23,28 @@
 
 namespace ce {
 
-int generic_blocks(int64_t S) {
+int generic_blocks(int64_t S, int sms) {
   int64_t want = (S + kGenericThreads - 1) / kGenericThreads;
-  const int64_t cap = 152 * 8;
-  return (int)(want < cap ? want : cap);
+  const int64_t cap = (int64_t)sms * 8;
+  return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+int sm_count(int device) {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  if (device < 0 && cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (device >= kMaxDevices) device = kMaxDevices - 1;
+  int n = cache[device].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[device].store(n, std::memory_order_relaxed);
+  return n;
 }
 
 // Lattice coordinates along a grid-stride walk s0, s0 + stride, ...: one
@@ -576,8 +595,8 @@ template cudaError_t launch_diag<double>(const DiagArgs<double>&, int, cudaStrea
 
 template <typename T, int NF>
 static cudaError_t launch_sync_nf(const DiagArgs<T>& a, cudaStream_t st) {
-  int64_t want = (a.count + 255) / 256;
-  int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  const int64_t want = (a.count + 255) / 256, cap = (int64_t)sm_count(-1) * 16;
+  int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
   switch (a.dims) {
     case 1: k_sync_u_range<T, NF, 1><<<blocks, 256, 0, st>>>(a); break;
@@ -663,8 +682,8 @@ __global__ void k_vhalf_to_f64(const T* __restrict__ f, const T* __restrict__ w,
 }
 
 static int conv_blocks(int64_t n) {
-  int64_t want = (n + 255) / 256;
-  return (int)(want < 152 * 16 ? (want < 1 ? 1 : want) : 152 * 16);
+  const int64_t want = (n + 255) / 256, cap = (int64_t)sm_count(-1) * 16;
+  return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
 }
 
 template <typename T>

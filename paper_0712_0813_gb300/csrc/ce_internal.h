@@ -184,7 +184,9 @@ struct ce_sim {
   double t = 0.0;
   int64_t step = 0;
   int kernel = CE_KERNEL_GENERIC;
+  int sms = 1;                 // streaming multiprocessors of the handle's device
   int generic_blocks = 1;
+  int diag_blocks_max = 8;     // grid cap of the diagnostics pass: 8 blocks per SM
   ce::SweepPlan plan{};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
   bool graphs_ok = true;
@@ -216,7 +218,10 @@ cudaError_t rows_launch(const ce_batch* b, int in, cudaStream_t st);
 void rows_free(ce_batch* b);
 
 constexpr int kGenericThreads = 256;
-int generic_blocks(int64_t S);
-constexpr int kDiagBlocksMax = 1216;   // 8 per SM on a 152-SM GB300
+// Grid of the generic kernel: one thread per site, at most 8 blocks per SM.
+int generic_blocks(int64_t S, int sms);
+// Streaming multiprocessors of a device (device < 0: the current one), read
+// once per device from cudaDevAttrMultiProcessorCount; 1 if it cannot be read.
+int sm_count(int device);
 
 }  // namespace ce

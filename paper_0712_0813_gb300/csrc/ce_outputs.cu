@@ -210,7 +210,7 @@ int ce_spectrum(ce_sim* s, int field, int nbins, double* k, double* power, doubl
     w->nbins_max = max_bins;
   }
   cufftSetStream(w->plan, s->stream);
-  const int cblocks = (int)std::min<int64_t>((s->S + 255) / 256, 152 * 8);
+  const int cblocks = (int)std::min<int64_t>((s->S + 255) / 256, (int64_t)s->sms * 8);
   if (f32)
     k_shifted_copy<float><<<cblocks, 256, 0, s->stream>>>(static_cast<const float*>(s->f[s->cur][field]),
                                                            static_cast<float*>(w->real), s->S);
@@ -276,7 +276,7 @@ int ce_sample_fields(ce_sim* s, const int64_t* sites, int64_t n, double* f, doub
     double* d_v = d_f + m * s->nf;
     e = cudaMemcpyAsync(d_sites, sites + k0, (size_t)m * 8, cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return ocuda(e, "ce_sample_fields: site upload");
-    const int blocks = (int)std::min<int64_t>((m + 255) / 256, 152 * 4);
+    const int blocks = (int)std::min<int64_t>((m + 255) / 256, (int64_t)s->sms * 4);
     if (s->prec == CE_F32) {
       SamplePtrs<float> p{};
       for (int i = 0; i < s->nf; ++i) {
