@@ -38,10 +38,47 @@ def _key(N, nfields, precision, expansion):
 
 def zchunk_candidates(N: int) -> list:
     if N >= 512:       # the grid is already many waves deep; a few short columns suffice
-        base = [0, 1, 2, 4, 8]
+        base = [0, 1, 2, 4, 8, 16]
     else:
         base = [0, 4, 6, 8, 10, 12, 14, 16, 19, 24, 32, 38]
     return [z for z in base if z == 0 or z <= N // 2]
+
+
+def tune_handle(sim, stream, N: int, *, steps: int = 40, warmup: int = 8, repeats: int = 2, zchunks=None,
+                variants=VARIANTS) -> list:
+    """Time every applicable (tile_rows, stages, zchunks) on an existing
+    z-sweep handle (its state advances by the timed steps); returns the table
+    (tile_rows, stages, zchunks, ms_per_step).  The handle is left on the
+    last candidate: replan it to the chosen plan."""
+    import torch
+    table, seen = [], set()
+    for rows, stages in variants:
+        for zc in (zchunks if zchunks is not None else zchunk_candidates(N)):
+            try:
+                sim.replan(rows, stages, zc)
+            except capi.CeError as e:
+                if e.code == capi.CE_EINVAL:
+                    continue          # this variant does not apply to the lattice
+                raise
+            plan = sim.sweep_plan
+            if plan in seen:          # "automatic" may coincide with an explicit count
+                continue
+            seen.add(plan)
+            sim.step(warmup)
+            best = float("inf")
+            for _ in range(repeats):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(steps)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / steps)
+            sim.synchronize()
+            table.append((plan[0], plan[1], plan[2], best))
+    if not table:
+        raise capi.CeError(capi.CE_EINVAL, "no z-sweep variant applies to this lattice")
+    return table
 
 
 def autotune_sweep(f0, u0, *, N: int, L: float, dt: float, nfields: int, q, expansion: bool,
@@ -56,33 +93,11 @@ def autotune_sweep(f0, u0, *, N: int, L: float, dt: float, nfields: int, q, expa
     if use_cache and key in _cache:
         return _cache[key]
     stream = torch.cuda.Stream()
-    table = []
     with capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nfields, q=q, expansion=expansion, phi0=phi0,
                          precision=precision, kernel="sweep", stream=stream.cuda_stream) as sim:
         sim.set_fields(f0, u0)
-        for rows, stages in variants:
-            for zc in (zchunks if zchunks is not None else zchunk_candidates(N)):
-                try:
-                    sim.replan(rows, stages, zc)
-                except capi.CeError as e:
-                    if e.code == capi.CE_EINVAL:
-                        continue          # this variant does not apply to the lattice
-                    raise
-                plan = sim.sweep_plan
-                sim.step(warmup)
-                best = float("inf")
-                for _ in range(repeats):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    sim.step(steps)
-                    e1.record(stream)
-                    e1.synchronize()
-                    best = min(best, e0.elapsed_time(e1) / steps)
-                sim.synchronize()
-                table.append((plan[0], plan[1], plan[2], best))
-    if not table:
-        raise capi.CeError(capi.CE_EINVAL, "no z-sweep variant applies to this lattice")
+        table = tune_handle(sim, stream, N, steps=steps, warmup=warmup, repeats=repeats, zchunks=zchunks,
+                            variants=variants)
     r, s_, z, ms = min(table, key=lambda t: t[3])
     res = TuneResult(r, s_, z, ms, table)
     _cache[key] = res
