@@ -398,8 +398,8 @@ def batched_leg(capi, torch, steps: int, warmup: int, seq_steps: int, hbm_peak: 
                 site_steps += W.sites(sp) * nsteps
         return site_steps / (t_ms / 1e3) / 1e9
 
-    fp64_seq = sequential("f64", seq_steps)
-    f32_seq = sequential("f32", seq_steps)
+    fp64_seq = sequential("f64", seq_steps) if seq_steps > 0 else None
+    f32_seq = sequential("f32", seq_steps) if seq_steps > 0 else None
     alg = 16 * 2 * total
     achieved = alg / (ms / 1e3 / steps) / 1e9
     return {"workload": "96 lattices: 32 x 1D 65536, 32 x 2D 1024^2, 32 x 3D side in {64..192}; 2 fields, "
@@ -407,7 +407,7 @@ def batched_leg(capi, torch, steps: int, warmup: int, seq_steps: int, hbm_peak: 
             "sites": total, "steps": steps, "ms_per_step": ms / steps, "items": info["items"],
             "sweep_len": tune["sweep_len"], "ctas_per_sm": tune["ctas_per_sm"], "autotune": tune["table"],
             "blocks": info["blocks"], "value_f32_batched": batched, "fp64_plain_sequential": fp64_seq,
-            "f32_plain_sequential": f32_seq, "batched_over_fp64_plain": batched / fp64_seq,
+            "f32_plain_sequential": f32_seq, "batched_over_fp64_plain": batched / fp64_seq if fp64_seq else None,
             "sequential_steps": seq_steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "kernel": "k_step_batched",
@@ -592,6 +592,40 @@ def shapes_mode(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> i
     return 0
 
 
+def single_mode(spec: str, steps: int, warmup: int) -> int:
+    """One lattice, one kernel: `dims,N,kernel[,precision[,fields]]` (kernel auto,
+    generic, sweep, rows or planes), 2 fields by default, expansion on, q = 1.2
+    (fields 4: q = 0.8, 5, 40), Courant dt.  Prints one JSON line with the time
+    per step (CUDA events) and the fraction of measured HBM the algorithmic
+    16 (FP32) / 32 (FP64) bytes per field and site reach.  Small cases of this
+    mode are what the ncu captures under profiles/ run."""
+    import torch
+    from paper_0712_0813_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_0712_0813_gb300 import capi
+    from paper_0712_0813_gb300.icgen import courant_dt, lattice_ics
+    parts = spec.split(",")
+    dims, N, kernel = int(parts[0]), int(parts[1]), parts[2]
+    precision = parts[3] if len(parts) > 3 else "f32"
+    nf = int(parts[4]) if len(parts) > 4 else 2
+    q = (1.2,) if nf == 2 else (0.8, 5.0, 40.0)[:nf - 1]
+    peak, _ = peaks()
+    S = N ** dims
+    f0, u0 = lattice_ics(dims, N, 20.0, nf, q=q, seed=3, backend="torch" if S >= 1 << 25 else "numpy")
+    stream = torch.cuda.Stream()
+    with capi.Simulation(dims=dims, N=N, L=20.0, dt=courant_dt(dims, N, 20.0, 1.0, q), nfields=nf, q=q,
+                         expansion=True, precision=precision, kernel=kernel, stream=stream.cuda_stream) as sim:
+        sim.set_fields(f0, u0)
+        us = _shape_timed(torch, stream, sim.step, steps, warmup)
+        sim.synchronize()
+        used = {1: "generic", 2: "sweep", 3: "rows", 4: "planes"}[sim.kernel]
+    alg = 4 * (4 if precision == "f32" else 8) * nf * S
+    print(json.dumps({"case": "single", "dims": dims, "N": N, "fields": nf, "precision": precision,
+                      "kernel": used, "steps": steps, "us_per_step": us, "gsite_per_s": S / us / 1e3,
+                      "frac": alg / (us * 1e-6) / 1e9 / peak}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -619,9 +653,15 @@ def main():
                     help="use the library's default launch plan instead of the autotuned one")
     ap.add_argument("--shapes", action="store_true",
                     help="per-shape timings of the batched and single-lattice kernels (JSON lines), then exit")
+    ap.add_argument("--single", default=None, metavar="DIMS,N,KERNEL[,PREC[,FIELDS]]",
+                    help="time one lattice on one kernel for --steps steps (JSON line), then exit")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the mixed-batch leg (--batch-steps, no one-at-a-time baselines), then exit")
     args = ap.parse_args()
     if args.shapes:
         return shapes_mode()
+    if args.single:
+        return single_mode(args.single, args.steps or 20, args.warmup)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     w = dict(WORKLOADS[args.workload])
@@ -658,6 +698,9 @@ def main():
     from paper_0712_0813_gb300 import capi
 
     hbm_peak, peak_kind = peaks()
+    if args.batch_only:
+        print(json.dumps({"batched_mix": batched_leg(capi, torch, args.batch_steps, 3, 0, hbm_peak)}), flush=True)
+        return 0
     S = w["N"] ** w["dims"]
     f0, u0 = make_inputs(w, rank)
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \

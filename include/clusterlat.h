@@ -71,13 +71,15 @@ extern "C" {
 /* ---- kernel selection (ce_config.kernel) ------------------------------ */
 #define CE_KERNEL_AUTO    0 /* FP32: z-sweep kernel where it applies; else the
                                row kernel for 2D sides >= 512 and 3D sides >= 64
-                               it takes; else generic.  FP64: generic (its
-                               two-pass form), or the z-sweep kernel when plan
-                               hints (tile_rows, stages, zchunks) are given    */
+                               it takes; else, in 3D, the plane-sweep kernel;
+                               else generic.  FP64: generic (its two-pass
+                               form), or the z-sweep kernel when plan hints
+                               (tile_rows, stages, zchunks) are given          */
 #define CE_KERNEL_GENERIC 1 /* one thread per site, any d and N              */
 #define CE_KERNEL_SWEEP   2 /* 3D z-sweep kernel (CE_EINVAL if it does not apply) */
 #define CE_KERNEL_ROWS    3 /* the batched row-sweep kernel on this one lattice:
                                any d, N a multiple of 4 (FP32) / 2 (FP64)      */
+#define CE_KERNEL_PLANES  4 /* 3D plane-sweep kernel with plain loads: any N   */
 
 /* ---- config flags ---------------------------------------------------- */
 #define CE_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt < 2/omega_max check       */
@@ -217,7 +219,7 @@ const char* ce_last_error(void);
 /* Bytes of device memory the handle holds (state + scratch). */
 int64_t ce_device_bytes(const ce_sim* sim);
 
-/* Which kernel ce_step launches: CE_KERNEL_GENERIC, _SWEEP or _ROWS. */
+/* Which kernel ce_step launches: CE_KERNEL_GENERIC, _SWEEP, _ROWS or _PLANES. */
 int ce_kernel_in_use(const ce_sim* sim);
 
 /* The z-sweep launch plan in use: tile rows, pipeline stages and z-chunks
@@ -253,9 +255,11 @@ int ce_load(ce_sim* sim, const char* path);
  * A batch groups existing handles (any mix of dimensions and sizes, same
  * precision and number of fields, fields already set) and advances all of
  * them together: each step is ONE launch of a persistent kernel whose CTAs
- * pull work items (row segments of one lattice, swept along its slowest axis)
- * from a queue; each lattice keeps its own scale factor, computed by the CTA
- * that completes that lattice's last item.  Per site the arithmetic is the
+ * pull work items (row segments of one 2D or 3D lattice, swept along its
+ * slowest axis) from a queue, followed, when the batch holds 1D lattices, by
+ * one launch that steps all of them (blocks of 16-byte site groups); each
+ * lattice keeps its own scale factor, computed by the CTA that completes that
+ * lattice's last item or block.  Per site the arithmetic is the
  * same fused staggered-leapfrog step as ce_step (Sec. III).  While a handle
  * belongs to a batch, ce_step and ce_set_fields on it return CE_ESTATE; the
  * read-out calls (ce_energy, ce_get_fields, ...) wait for the batch first.
@@ -285,7 +289,8 @@ int ce_batch_synchronize(ce_batch* b);
  * Errors: CE_EINVAL (NULL, n too small), CE_ECUDA. */
 int ce_batch_status(ce_batch* b, int* status, int n);
 
-/* Members, work items per step, persistent CTAs, total sites. */
+/* Members, work units per step (items of the persistent kernel plus blocks of
+ * the 1D launch), persistent CTAs, total sites. */
 int ce_batch_info(const ce_batch* b, int* members, int* items, int* blocks, int64_t* sites);
 
 /* Release the batch (members stay valid with their current state).  NULL-safe. */

@@ -19,7 +19,7 @@ from . import build as _build
 CE_OK, CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ETIMEOUT, CE_ENONFINITE, CE_ESTATE = 0, -1, -2, -3, -4, -5, -6
 CE_F64, CE_F32 = 0, 1
 CE_VEL_SYNC, CE_VEL_STAGGERED = 0, 1
-CE_KERNEL_AUTO, CE_KERNEL_GENERIC, CE_KERNEL_SWEEP, CE_KERNEL_ROWS = 0, 1, 2, 3
+CE_KERNEL_AUTO, CE_KERNEL_GENERIC, CE_KERNEL_SWEEP, CE_KERNEL_ROWS, CE_KERNEL_PLANES = 0, 1, 2, 3, 4
 CE_FLAG_ALLOW_UNSTABLE_DT = 1
 CE_FLAG_TEST_TMA_STALL = 2
 
@@ -168,7 +168,7 @@ def ce_create(dims: int, N: int, L: float, dt: float, nfields: int = 2, q=(1.2,)
     cfg.phi0 = float(phi0)
     cfg.precision = {"f64": CE_F64, "f32": CE_F32}.get(precision, precision)
     cfg.kernel = {"auto": CE_KERNEL_AUTO, "generic": CE_KERNEL_GENERIC, "sweep": CE_KERNEL_SWEEP,
-                  "rows": CE_KERNEL_ROWS}.get(kernel, kernel)
+                  "rows": CE_KERNEL_ROWS, "planes": CE_KERNEL_PLANES}.get(kernel, kernel)
     cfg.flags = (CE_FLAG_ALLOW_UNSTABLE_DT if allow_unstable_dt else 0) | int(flags)
     cfg.tile_rows, cfg.stages, cfg.zchunks = int(tile_rows), int(stages), int(zchunks)
     if stream is not None:

@@ -6,17 +6,16 @@
 // w_out = v + dt (lap g - dV/df(g)), f_out = g, plus the sums of
 // (g(x+e_d) - g(x))^2 and V(g) that advance each lattice's own scale factor.
 //
-// Work decomposition.  Every lattice of the batch is cut into work items of
-// about the same size, and a CTA of 8 warps takes one item, swept along the
-// lattice's slowest axis (z in 3D, y in 2D; 1D items have no sweep).  3D: rows
-// of one segment of 32, 16 or 8 lanes x VX sites (VX = 16 B / sizeof(T); the
-// width that pads a row of N sites least), so a warp holds 1, 2 or 4 rows;
-// 2D/1D: each warp owns one 32-lane segment of a row.  Each plane of the item
-// (f and w of every field, in 3D with the two y-halo rows and the x-halo
-// columns) is staged in a shared-memory ring: 3D planes by TMA tensor copies
-// from per-lattice tensor maps (one lane per field and array issues the boxes,
-// an mbarrier per slot signals their arrival), 2D/1D planes by per-thread
-// cp.async.  One block barrier per plane publishes the landed plane and frees
+// Work decomposition.  Every 2D and 3D lattice of the batch is cut into work
+// items of about the same size, and a CTA of 8 warps takes one item, swept
+// along the lattice's slowest axis (z in 3D, y in 2D).  3D: rows of one segment
+// of 32, 16 or 8 lanes x VX sites (VX = 16 B / sizeof(T); the width that pads a
+// row of N sites least), so a warp holds 1, 2 or 4 rows; 2D: each warp owns one
+// 32-lane segment of a row.  Each plane of the item (f and w of every field, in
+// 3D with the two y-halo rows and the x-halo columns) is staged in a
+// shared-memory ring: 3D planes by TMA tensor copies from per-lattice tensor
+// maps (one lane per field and array issues the boxes, an mbarrier per slot
+// signals their arrival), 2D planes by per-thread cp.async.  One block barrier per plane publishes the landed plane and frees
 // the slot read two planes earlier.  Sweep-axis neighbours stay in registers,
 // x-neighbours come from the adjacent lane by shuffle and from the staged halo,
 // y-neighbours from the staged rows.  Segments may be partial (N not a multiple
@@ -27,8 +26,18 @@
 // last item of a lattice combines that lattice's item partials (all its
 // threads, in an order fixed by the lattice's item count) and advances its a,
 // a', a'' -- nobody waits for anybody.  The last CTA to
-// leave resets the queue for the next launch.  One launch advances every
-// lattice by one step; step loops are CUDA graphs of 32 launches.
+// leave resets the queue for the next launch.
+//
+// 1D lattices have no plane to sweep and little work per row segment: staged
+// one segment span at a time they streamed HBM at a quarter of the bandwidth.
+// They run in a second kernel, k_step_1d_members (the single-lattice 1D
+// kernel's per-group arithmetic, 16-byte loads and stores straight from HBM,
+// each block kG1d x 256 groups of VX sites of one lattice); each lattice's last
+// block combines its blocks' sums and advances its scale factor.  The 1D and
+// the 2D/3D lattices share nothing, so the 1D launches go on a second stream
+// forked from the batch's stream (and joined back after the step loop, also
+// inside the captured graphs): they run while the persistent kernel leaves SMs
+// free, at its tail.  Step loops are CUDA graphs of 32 steps.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -56,6 +65,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kMapTypes = 7;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: bound of every device-side wait
 constexpr int kBatchGraphSteps = 32;
+constexpr int kG1d = 4;   // groups of VX sites per thread of the 1D launch
 
 template <typename T>
 struct BMember {
@@ -65,7 +75,7 @@ struct BMember {
   int* status;
   unsigned int* done;      // items of this lattice completed in the running launch
   double* partials;        // 2 doubles per item of this lattice
-  int dims, N, p0, first_item, n_items, update_scalars;
+  int dims, N, p0, first_item, n_items, update_scalars;   // 1D: n_items = blocks of the 1D launch
   int seg_log2;            // 3D: log2 of the lanes per row segment (5, 4 or 3: 1, 2 or 4 rows per warp)
   const CUtensorMap* tmaps;  // 3D: tensor maps of f, w (see kMapTypes), device memory; else null
   T inv_dx2, dt, q[3];
@@ -76,7 +86,7 @@ struct BItem {
   int member;
   int x0;      // first x site of the (first) segment
   int y0;      // first row (3D items)
-  int s0, s1;  // sweep range: z (3D), y (2D); [0, 1) for 1D
+  int s0, s1;  // sweep range: z (3D), y (2D)
 };
 
 template <typename T, int VX>
@@ -86,31 +96,6 @@ __device__ __forceinline__ void st16(T* p, const T (&o)[VX]) {
   } else {
     __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
   }
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Asynchronous global -> shared copies (no registers held while in flight).
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_small(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)),
-               "l"(__cvta_generic_to_global(src)), "n"(BYTES)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int PENDING>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
 template <typename T, int VX>
@@ -129,7 +114,7 @@ __device__ __forceinline__ void lds16(const T* p, T (&o)[VX]) {
 // segment is LR = 32, 16 or 8 lanes x VX sites, so a warp holds 1, 2 or 4 rows
 // and an item rows = 8, 16 or 32 rows: (rows + 2) W sites, which is 8 SEG + 2 W),
 // then the left and the right x-halo columns, 16 bytes (VX sites) per row each,
-// as TMA delivers them.  2D/1D: row 0 holds the 8 warps' segments side by side
+// as TMA delivers them.  2D: row 0 holds the 8 warps' segments side by side
 // and the span's two halo elements follow the 10th row.  The largest 3D case
 // (10 rows of 32 VX plus 2 x 8 x VX halo sites, or 34 rows of 8 VX plus
 // 2 x 32 x VX) sizes the stage; ARR x sizeof(T) is a multiple of 128 bytes, so
@@ -153,16 +138,17 @@ constexpr size_t batch_smem() {
 // 3D planes arrive by TMA (one lane per array issues one or two row boxes and two
 // x-halo column boxes from the member's tensor maps; full[slot] completes
 // when the bytes have landed, every thread waits on it with a bounded wait and
-// keeps the slot's phase in bit slot of ph); 2D/1D planes by per-thread
+// keeps the slot's phase in bit slot of ph); 2D planes by per-thread
 // cp.async.  Returns false when a wait ran out (the caller stops).
 // DIMS 3: a row segment is LR = 2^seg_log2 lanes x VX sites; lane l of warp w
 // owns row r = w (32 / LR) + l / LR of the item, sites (l mod LR) VX .. + VX - 1
 // of the segment, and sweeps z (x-neighbour shuffles stay inside each LR-lane
 // group); DIMS 2: warp w owns segment w of an 8-segment span of one row and
-// sweeps y; DIMS 1: the same span, one "plane".
+// sweeps y.
 template <typename T, int NF, int NST, int DIMS>
 __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int in, const BItem& it, T* smem,
                                          uint64_t* full, uint32_t& ph, int warp, int lane, T& g2loc, T& vloc) {
+  static_assert(DIMS == 2 || DIMS == 3, "1D lattices run in k_step_1d_members");
   constexpr int VX = Stage<T>::VX, SEG = Stage<T>::SEG, ARR = Stage<T>::ARR;
   const int N = m->N;
   const int64_t NN = (int64_t)N * N;
@@ -192,12 +178,12 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
   }
   const bool valid = rvalid && sub < nvl;
   const int col = sub * VX;                      // column inside the lane's segment
-  const int span_end = min(N, it.x0 + 8 * SEG);  // 2D/1D: end of the CTA's span
+  const int span_end = min(N, it.x0 + 8 * SEG);  // 2D: end of the CTA's span
   const int last_warp = (span_end - it.x0 + SEG - 1) / SEG - 1;
   const int y = it.y0 + r;                       // 3D row
   const auto wrap = [&](int v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
-  const int n = DIMS == 1 ? 1 : it.s1 - it.s0 + 2;
-  const auto plane = [&](int j) { return DIMS == 1 ? 0 : wrap(it.s0 - 1 + j); };
+  const int n = it.s1 - it.s0 + 2;
+  const auto plane = [&](int j) { return wrap(it.s0 - 1 + j); };
   const T c = (T)m->slot[in].c;
   const T dd = m->dt, kk = m->dt, idx2 = m->inv_dx2;
   T q[3] = {m->q[0], m->q[1], m->q[2]};
@@ -244,7 +230,7 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
       tma_load_3d(st + hbase + rows3 * VX, mp + hts, xr, y0, zz, &full[slot]);
       return;
     } else {
-      const int64_t poff = DIMS == 2 ? (int64_t)plane(j) * N : 0;
+      const int64_t poff = (int64_t)plane(j) * N;
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
 #pragma unroll
@@ -360,8 +346,7 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
       for (int i = 0; i < NF; ++i) lap[i][k] = fmaT(kk, lap[i][k] - dv[i], vc[i][k]);
     }
     if (valid) {
-      const int64_t here = DIMS == 3 ? (int64_t)zj * NN + (y * N + x0 + col)
-                                     : (DIMS == 2 ? (int64_t)zj * N + x0 + col : (int64_t)x0 + col);
+      const int64_t here = DIMS == 3 ? (int64_t)zj * NN + (y * N + x0 + col) : (int64_t)zj * N + x0 + col;
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
         st16<T, VX>(m->f[in ^ 1][i] + here, gc[i]);
@@ -386,7 +371,7 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
   };
 
   // prologue: fill the ring (3D: every thread's fence, then the barrier, order
-  // a previous 2D/1D item's cp.async writes into the same slots before these
+  // a previous 2D item's cp.async writes into the same slots before these
   // TMA writes)
   if constexpr (DIMS == 3) {
     fence_proxy_async_smem();
@@ -411,16 +396,7 @@ __device__ __forceinline__ bool run_item(const BMember<T>* __restrict__ m, int i
     }
     return true;
   };
-  if constexpr (DIMS == 1) {
-    cp_wait<0>();
-    __syncthreads();
-    T none[NF][VX];
-    if (wvalid) {
-      own_g(0, gc);
-      update(0, none);
-    }
-    return true;
-  } else {
+  {
     if constexpr (DIMS == 3) {
       if (!landed(0) || !landed(1)) return false;
     } else {
@@ -488,15 +464,14 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
     T g2loc = T(0), vloc = T(0);
     bool ok;
     if (m->dims == 3) ok = run_item<T, NF, NST, 3>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
-    else if (m->dims == 2) ok = run_item<T, NF, NST, 2>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
-    else ok = run_item<T, NF, NST, 1>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
+    else ok = run_item<T, NF, NST, 2>(m, in, it, smem, s_full, ph, warp, lane, g2loc, vloc);
     if (!ok) {   // a bounded wait ran out: report it on the lattice and stop this CTA
       if (threadIdx.x == 0) atomicCAS(m->status, CE_OK, CE_ETIMEOUT);
       break;
     }
     if (m->update_scalars) {
-      double g2 = (double)g2loc, pot = (double)vloc;
-      block_sum2(g2, pot);
+      double g2, pot;
+      block_sum2_t<T>(g2loc, vloc, g2, pot);
       if (threadIdx.x == 0) {
         const int k = itx - m->first_item;
         m->partials[2 * k] = g2;
@@ -537,6 +512,75 @@ __global__ void __launch_bounds__(kThreads, NF <= 2 ? 2 : 1) k_step_batched(cons
   }
 }
 
+// One step of the batch's 1D lattices: blockIdx.y picks the lattice (m1d
+// lists the 1D members), blockIdx.x a block of kG1d x kThreads groups of VX
+// sites inside it (thread t takes groups t, t + kThreads, ...; blocks past the
+// lattice's n_items leave at once).  Per site the arithmetic is
+// step1d_group's (that of the single-lattice 1D kernel); a thread's sums stay
+// in T over its kG1d groups (16 sites in FP32, as in the other step kernels),
+// the block adds them with block_sum2_t into the lattice's partials, and the
+// lattice's last block adds those in block order (thread t takes blocks t, t +
+// kThreads, ..., then a fixed tree) and advances its a, a', a''.  A lattice's
+// blocks and the order of its sums depend on its N alone, so its result does
+// not depend on the mix.
+template <typename T, int NF>
+__global__ void __launch_bounds__(kThreads) k_step_1d_members(const BMember<T>* __restrict__ members,
+                                                              const int* __restrict__ m1d, int par) {
+  constexpr int VX = 16 / sizeof(T);
+  const BMember<T>* m = members + m1d[blockIdx.y];
+  const int nb = m->n_items;
+  if ((int)blockIdx.x >= nb) return;
+  const int in = m->p0 ^ par;
+  const int64_t N = m->N, groups = N / VX;
+  const T q[3] = {m->q[0], m->q[1], m->q[2]};
+  const T c = (T)m->slot[in].c;
+  const T* f_in[4];
+  const T* w_in[4];
+  T* f_out[4];
+  T* w_out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f_in[i] = m->f[in][i];
+    w_in[i] = m->w[in][i];
+    f_out[i] = m->f[in ^ 1][i];
+    w_out[i] = m->w[in ^ 1][i];
+  }
+  T g2loc = T(0), vloc = T(0);
+  const int64_t k0 = (int64_t)blockIdx.x * (kG1d * kThreads) + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < kG1d; ++r) {
+    const int64_t k = k0 + (int64_t)r * kThreads;
+    if (k < groups)
+      step1d_group<T, NF>(f_in, w_in, f_out, w_out, N, k, c, m->dt, m->dt, m->inv_dx2, q, g2loc, vloc);
+  }
+  if (!m->update_scalars) return;   // the same for every thread of the block
+  __shared__ int s_last;
+  double g2, pot;
+  block_sum2_t<T>(g2loc, vloc, g2, pot);
+  if (threadIdx.x == 0) {
+    m->partials[2 * blockIdx.x] = g2;
+    m->partials[2 * blockIdx.x + 1] = pot;
+    __threadfence();
+    s_last = atomicAdd(m->done, 1u) == (unsigned int)(nb - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double G = 0.0, V = 0.0;
+  for (int j = threadIdx.x; j < nb; j += kThreads) {
+    G += __ldcg(m->partials + 2 * j);
+    V += __ldcg(m->partials + 2 * j + 1);
+  }
+  block_sum2(G, V);
+  if (threadIdx.x == 0) {
+    DevScalars out;
+    scale_factor_update(m->slot[in], out, G * m->half_inv_dx2 * m->inv_S, V * m->inv_S, m->ddt, m->kappa2,
+                        m->status);
+    m->slot[in ^ 1] = out;
+    *m->done = 0u;
+  }
+}
+
 }  // namespace
 }  // namespace ce
 
@@ -549,7 +593,12 @@ struct ce_batch {
   void* d_items = nullptr;
   unsigned int* d_queue = nullptr;   // [0] head, [1] exit count
   unsigned int* d_done = nullptr;    // per member
-  double* d_partials = nullptr;      // 2 per item
+  double* d_partials = nullptr;      // 2 per item (and per block of a 1D member)
+  int* d_m1d = nullptr;              // indices of the 1D members
+  int n1d = 0, bx1d = 0;             // 1D members; blocks of the largest one
+  int n_units = 0;                   // items plus the 1D members' blocks
+  cudaStream_t side = nullptr;       // the 1D launches when the batch also has 2D/3D lattices
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* d_maps = nullptr;            // tensor maps of the 3D members
   int n_items = 0, blocks = 0, par = 0, sweep_len = 32;
   int ctas_per_sm = 0;               // cap on resident CTAs per SM (0: as many as fit)
@@ -573,28 +622,48 @@ int bcuda(cudaError_t e, const char* what) {
 
 constexpr int kBatchStages = 4;
 
+// One step: the persistent launch (2D/3D members) on the batch's stream and
+// the 1D launch on `st1d` (the side stream, or the batch's stream itself).
 template <typename T, int NF>
-cudaError_t launch_nf(const ce_batch* b, int par) {
+cudaError_t launch_nf(const ce_batch* b, int par, cudaStream_t st1d) {
   const auto* mem = static_cast<const ce::BMember<T>*>(b->d_members);
   const auto* it = static_cast<const ce::BItem*>(b->d_items);
   constexpr size_t smem = ce::batch_smem<T, NF, kBatchStages>();
-  ce::k_step_batched<T, NF, kBatchStages><<<b->blocks, ce::kThreads, smem, b->stream>>>(mem, it, b->n_items,
-                                                                                         b->d_queue, par);
+  if (b->n_items > 0)
+    ce::k_step_batched<T, NF, kBatchStages><<<b->blocks, ce::kThreads, smem, b->stream>>>(mem, it, b->n_items,
+                                                                                           b->d_queue, par);
+  if (b->n1d > 0)
+    ce::k_step_1d_members<T, NF><<<dim3(b->bx1d, b->n1d), ce::kThreads, 0, st1d>>>(mem, b->d_m1d, par);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_t(const ce_batch* b, int par) {
+cudaError_t launch_t(const ce_batch* b, int par, cudaStream_t st1d) {
   switch (b->nf) {
-    case 1: return launch_nf<T, 1>(b, par);
-    case 2: return launch_nf<T, 2>(b, par);
-    case 3: return launch_nf<T, 3>(b, par);
-    default: return launch_nf<T, 4>(b, par);
+    case 1: return launch_nf<T, 1>(b, par, st1d);
+    case 2: return launch_nf<T, 2>(b, par, st1d);
+    case 3: return launch_nf<T, 3>(b, par, st1d);
+    default: return launch_nf<T, 4>(b, par, st1d);
   }
 }
 
 cudaError_t launch_batch(const ce_batch* b, int par) {
-  return b->prec == CE_F32 ? launch_t<float>(b, par) : launch_t<double>(b, par);
+  cudaStream_t st1d = b->side ? b->side : b->stream;
+  return b->prec == CE_F32 ? launch_t<float>(b, par, st1d) : launch_t<double>(b, par, st1d);
+}
+
+// Fork the side stream from the batch's stream / join it back (no-ops for a
+// batch without a side stream).  Under stream capture these become the
+// graph's fork and join edges.
+cudaError_t fork_side(const ce_batch* b) {
+  if (!b->side) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+  return e == cudaSuccess ? cudaStreamWaitEvent(b->side, b->ev_fork, 0) : e;
+}
+cudaError_t join_side(const ce_batch* b) {
+  if (!b->side) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(b->ev_join, b->side);
+  return e == cudaSuccess ? cudaStreamWaitEvent(b->stream, b->ev_join, 0) : e;
 }
 
 template <typename T, int NF>
@@ -622,9 +691,12 @@ cudaError_t batch_prepare(int prec, int nf, int* per_sm) {
 }
 
 
-// Cut every member into items of about kWarps x 32 x VX x sweep_len sites.
+// Cut every 2D and 3D member into items of about kWarps x 32 x VX x sweep_len
+// sites; a 1D member gets ceil(N / VX / kThreads) blocks of the 1D launch
+// (listed in m1d).
 template <typename T>
-void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce::BItem>& items) {
+void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce::BItem>& items,
+                  std::vector<int>& m1d) {
   constexpr int VX = 16 / sizeof(T);
   constexpr int SEG = 32 * VX;
   struct Work {
@@ -652,17 +724,14 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
       for (int x0 = 0; x0 < N; x0 += ce::kWarps * SEG)
         for (int y0 = 0; y0 < N; y0 += L)
           add(x0, 0, y0, std::min(N, y0 + L), (int64_t)std::min(ce::kWarps * SEG, N - x0) * (std::min(N, y0 + L) - y0));
-    } else {
-      for (int x0 = 0; x0 < N; x0 += ce::kWarps * SEG) add(x0, 0, 0, 1, (int64_t)std::min(ce::kWarps * SEG, N - x0));
     }
   }
   // items of a member stay contiguous (their partials are indexed from first_item);
   // members are ordered by their largest item so the queue hands out big work first
   std::vector<size_t> order(b->members.size());
   for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) {
-    return per[a].front().cost * (int64_t)per[a].size() > per[c].front().cost * (int64_t)per[c].size();
-  });
+  const auto weight = [&](size_t k) { return per[k].empty() ? 0 : per[k].front().cost * (int64_t)per[k].size(); };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return weight(a) > weight(c); });
   mem.resize(b->members.size());
   for (size_t k : order) {
     const ce_sim* s = b->members[k];
@@ -682,6 +751,11 @@ void build_tables(ce_batch* b, std::vector<ce::BMember<T>>& mem, std::vector<ce:
     m.p0 = s->cur ^ b->par;
     m.first_item = (int)items.size();
     m.n_items = (int)per[k].size();
+    if (s->dims == 1) {
+      const int64_t per_block = (int64_t)ce::kG1d * ce::kThreads;
+      m.n_items = (int)((s->N / VX + per_block - 1) / per_block);
+      m1d.push_back((int)k);
+    }
     m.update_scalars = s->cfg.expansion ? 1 : 0;
     m.inv_dx2 = (T)(1.0 / (s->dx * s->dx));
     m.dt = (T)s->cfg.dt;
@@ -761,12 +835,28 @@ template <typename T>
 int upload_tables(ce_batch* b) {
   std::vector<ce::BMember<T>> mem;
   std::vector<ce::BItem> items;
-  // partial-sum slots are assigned after the item count is known
-  build_tables<T>(b, mem, items);
+  std::vector<int> m1d;
+  // partial-sum slots are assigned after the item count is known: the items'
+  // first, then each 1D member's blocks
+  build_tables<T>(b, mem, items, m1d);
   b->n_items = (int)items.size();
-  cudaError_t e = cudaMalloc(&b->d_partials, sizeof(double) * 2 * std::max(1, b->n_items));
+  b->n1d = (int)m1d.size();
+  int64_t slots = b->n_items;
+  for (int k : m1d) {
+    mem[k].first_item = (int)slots;
+    slots += mem[k].n_items;
+    b->bx1d = std::max(b->bx1d, mem[k].n_items);
+  }
+  b->n_units = (int)slots;
+  cudaError_t e = cudaMalloc(&b->d_partials, sizeof(double) * 2 * std::max<int64_t>(1, slots));
   if (e != cudaSuccess) return bcuda(e, "ce_batch_create: partials");
   for (auto& m : mem) m.partials = b->d_partials + 2 * (int64_t)m.first_item;
+  if (b->n1d > 0) {
+    e = cudaMalloc(&b->d_m1d, sizeof(int) * m1d.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_m1d, m1d.data(), sizeof(int) * m1d.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(e, "ce_batch_create: 1D member list");
+  }
   if (int rc = encode_maps<T>(b, mem)) return rc;
   e = cudaMalloc(&b->d_members, sizeof(ce::BMember<T>) * mem.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(ce::BItem) * std::max<size_t>(1, items.size()));
@@ -786,6 +876,10 @@ void release(ce_batch* b) {
   if (b->d_queue) cudaFree(b->d_queue);
   if (b->d_partials) cudaFree(b->d_partials);
   if (b->d_maps) cudaFree(b->d_maps);
+  if (b->d_m1d) cudaFree(b->d_m1d);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -794,12 +888,13 @@ cudaError_t ensure_batch_graph(ce_batch* b, int start) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
-  cudaError_t el = cudaSuccess;
+  cudaError_t el = fork_side(b);
   int par = start;
   for (int k = 0; k < ce::kBatchGraphSteps && el == cudaSuccess; ++k) {
     el = launch_batch(b, par);
     par ^= 1;
   }
+  if (el == cudaSuccess) el = join_side(b);
   e = cudaStreamEndCapture(b->stream, &g);
   if (el != cudaSuccess || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -969,6 +1064,16 @@ int ce_batch_create(ce_sim* const* sims, int n, int sweep_len, int ctas_per_sm, 
     return bcuda(e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "ce_batch_create: occupancy");
   }
   b->blocks = std::max(1, std::min(per_sm * sms, b->n_items));
+  if (b->n1d > 0 && b->n_items > 0) {
+    e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      release(b);
+      delete b;
+      return bcuda(e, "ce_batch_create: side stream");
+    }
+  }
   for (ce_sim* s : b->members) s->batch = b;
   *out = b;
   return CE_OK;
@@ -993,11 +1098,17 @@ int ce_batch_step(ce_batch* b, int64_t n) {
     advance_members(b, ce::kBatchGraphSteps);
     n -= ce::kBatchGraphSteps;
   }
-  for (int64_t k = 0; k < n; ++k) {
-    e = launch_batch(b, b->par);
-    if (e != cudaSuccess) return bcuda(e, "ce_batch_step: launch");
-    b->par ^= 1;
-    advance_members(b, 1);
+  if (n > 0) {
+    e = fork_side(b);
+    if (e != cudaSuccess) return bcuda(e, "ce_batch_step: fork");
+    for (int64_t k = 0; k < n; ++k) {
+      e = launch_batch(b, b->par);
+      if (e != cudaSuccess) return bcuda(e, "ce_batch_step: launch");
+      b->par ^= 1;
+      advance_members(b, 1);
+    }
+    e = join_side(b);
+    if (e != cudaSuccess) return bcuda(e, "ce_batch_step: join");
   }
   return CE_OK;
 }
@@ -1035,7 +1146,7 @@ int ce_batch_status(ce_batch* b, int* status, int n) {
 int ce_batch_info(const ce_batch* b, int* members, int* items, int* blocks, int64_t* sites) {
   if (!b || !members || !items || !blocks || !sites) return bfail(CE_EINVAL, "ce_batch_info: NULL argument");
   *members = (int)b->members.size();
-  *items = b->n_items;
+  *items = b->n_units;
   *blocks = b->blocks;
   *sites = b->sites;
   return CE_OK;

@@ -85,7 +85,7 @@ int validate(const ce_config* c, int64_t* S_out) {
   for (int i = 0; i + 1 < c->nfields; ++i)
     if (!(c->q[i] >= 0.0) || !std::isfinite(c->q[i])) return fail(CE_EINVAL, "ce_create: q_i must be finite and >= 0");
   if (c->precision != CE_F64 && c->precision != CE_F32) return fail(CE_EINVAL, "ce_create: precision must be CE_F64 or CE_F32");
-  if (c->kernel < CE_KERNEL_AUTO || c->kernel > CE_KERNEL_ROWS) return fail(CE_EINVAL, "ce_create: unknown kernel");
+  if (c->kernel < CE_KERNEL_AUTO || c->kernel > CE_KERNEL_PLANES) return fail(CE_EINVAL, "ce_create: unknown kernel");
   if (c->expansion != 0 && c->expansion != 1) return fail(CE_EINVAL, "ce_create: expansion must be 0 or 1");
   if (!!c->alloc != !!c->release) return fail(CE_EINVAL, "ce_create: alloc and release hooks go together");
   if (!std::isfinite(c->phi0_over_mpl) || !std::isfinite(c->phi0)) return fail(CE_EINVAL, "ce_create: non-finite phi0");
@@ -149,6 +149,7 @@ cudaError_t launch_one_step(const ce_sim* s, int in, bool half_kick) {
   if (s->kernel == CE_KERNEL_ROWS && !half_kick) return ce::rows_launch(s->rows, in, s->stream);
   const ce::StepArgs<T> a = make_step_args<T>(s, in, half_kick);
   if (s->kernel == CE_KERNEL_SWEEP) return ce::launch_step_sweep<T>(a, s->plan, s->stream);
+  if (s->kernel == CE_KERNEL_PLANES) return ce::launch_step_planes<T>(a, s->planes, s->stream);
   return ce::launch_step_generic<T>(a, s->generic_blocks, s->stream);
 }
 
@@ -305,6 +306,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const bool rows_ok = cfg->N % (cfg->precision == CE_F32 ? 4 : 2) == 0;
   if (cfg->kernel == CE_KERNEL_ROWS && !rows_ok)
     return fail(CE_EINVAL, "ce_create: the row kernel needs N a multiple of 4 (FP32) or 2 (FP64)");
+  if (cfg->kernel == CE_KERNEL_PLANES && cfg->dims != 3)
+    return fail(CE_EINVAL, "ce_create: the plane-sweep kernel needs dims == 3");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {
@@ -324,8 +327,9 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
   // Automatic choice.  FP32: the z-sweep kernel where it applies, else the row
-  // kernel for 2D and 3D lattices it takes, else the generic kernel (1D
-  // lattices, odd and small sides).  FP64 is bound by the FP64 rate, and there
+  // kernel for 2D and 3D lattices it takes, else in 3D the plane-sweep kernel
+  // (odd and small sides), else the generic kernel (1D lattices, 2D sides the
+  // row kernel does not take).  FP64 is bound by the FP64 rate, and there
   // the generic kernel's two-pass form (each site's g formed once) measured
   // faster than both the z-sweep kernel (256^3: 1090 against 1141 us, tuned
   // plan) and the row kernel (288^3: 1540 against 2967 us): the generic kernel,
@@ -333,11 +337,13 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const bool sweep_hinted = cfg->tile_rows != 0 || cfg->stages != 0 || cfg->zchunks != 0;
   const bool rows_auto = rows_ok && cfg->precision == CE_F32 && cfg->dims >= 2 &&
                          cfg->N >= (cfg->dims == 3 ? kRowsMinN3 : kRowsMinN2);
+  const bool planes_auto = cfg->precision == CE_F32 && cfg->dims == 3;
   if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
   else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
+  else if (cfg->kernel == CE_KERNEL_PLANES) s->kernel = CE_KERNEL_PLANES;
   else if (sweep_ok && (cfg->precision == CE_F32 || sweep_hinted || cfg->kernel == CE_KERNEL_SWEEP))
     s->kernel = CE_KERNEL_SWEEP;
-  else s->kernel = rows_auto ? CE_KERNEL_ROWS : CE_KERNEL_GENERIC;
+  else s->kernel = rows_auto ? CE_KERNEL_ROWS : (planes_auto ? CE_KERNEL_PLANES : CE_KERNEL_GENERIC);
   cudaGetDevice(&s->device);
   s->sms = ce::sm_count(s->device);
   s->generic_blocks = ce::generic_blocks(S, s->sms);
@@ -379,7 +385,12 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
     const int64_t tx = s->prec == CE_F32 ? 128 : 64;
     sweep_blocks = std::max<int64_t>((int64_t)s->plan.gx * s->plan.gy * s->plan.gz, (s->N / tx) * (s->N / 4) * (s->N / 2));
   }
-  int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, sweep_blocks), 1);
+  int64_t planes_blocks = 0;
+  if (s->kernel == CE_KERNEL_PLANES) {
+    s->planes = ce::planes_plan(s->N, s->nf, s->prec, s->sms);
+    planes_blocks = (int64_t)s->planes.gx * s->planes.gy * s->planes.gz;
+  }
+  int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, std::max(sweep_blocks, planes_blocks)), 1);
   int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)s->diag_blocks_max * 17);
   s->partials = static_cast<double*>(dalloc(s, (size_t)plen * 8));
   s->aux = static_cast<ce::DevAux*>(dalloc(s, sizeof(ce::DevAux)));

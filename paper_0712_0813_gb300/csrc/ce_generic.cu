@@ -119,8 +119,11 @@ __global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs
   const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
   const int64_t N = p.N, S = p.S;
   T q[3] = {p.q[0], p.q[1], p.q[2]};
-  double grad2 = 0.0, pot = 0.0;   // flushed from the T partials every 16 sites
-  T g2loc = T(0), vloc = T(0);
+  // sums of the step's global energies: 16 sites in T, then into a second T
+  // accumulator, converted to FP64 once per thread.  A flush into FP64 every
+  // 16 sites was if-converted into the site loop, which put a float-to-double
+  // conversion and an FP64 add per sum and site on GB300's narrow FP64 pipe.
+  T g2acc = T(0), vacc = T(0), g2loc = T(0), vloc = T(0);
   int since_flush = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,18 +161,14 @@ __global__ void __launch_bounds__(kGenericThreads) k_step_generic(const StepArgs
       p.f_out[i][s] = g[i];
     }
     if (++since_flush == 16) {
-      grad2 += (double)g2loc;
-      pot += (double)vloc;
+      g2acc += g2loc;
+      vacc += vloc;
       g2loc = T(0);
       vloc = T(0);
       since_flush = 0;
     }
   }
-  if (p.update_scalars) {
-    grad2 += (double)g2loc;
-    pot += (double)vloc;
-    finish_step_block(p, grad2, pot);
-  }
+  if (p.update_scalars) finish_step_block(p, (double)g2acc + (double)g2loc, (double)vacc + (double)vloc);
 }
 
 // FP64 in 2D and 3D, two passes.  In FP64 the step is bound by GB300's FP64
@@ -232,106 +231,34 @@ __global__ void __launch_bounds__(kGenericThreads) k_kick_from_g(const StepArgs<
   if (p.update_scalars) finish_step_block(p, grad2, pot);
 }
 
-// 16 bytes of consecutive sites: VX = 16 / sizeof(T) values, one vector access.
-template <typename T, int VX>
-__device__ __forceinline__ void ldg16(const T* p, T (&o)[VX]) {
-  if constexpr (sizeof(T) == 4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  } else {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    o[0] = v.x; o[1] = v.y;
-  }
-}
-template <typename T, int VX>
-__device__ __forceinline__ void stcs16(T* p, const T (&o)[VX]) {
-  if constexpr (sizeof(T) == 4) {
-    __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
-  } else {
-    __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
-  }
-}
-
-// The 1D step for N a multiple of VX = 16 / sizeof(T): each thread takes VX
-// consecutive sites with 16-byte loads and stores, and the sites on either side
-// of them (periodic wrap) with scalar loads that the neighbouring threads'
-// vectors already brought into L1.  Each site's g is formed once per field and
-// shared by its two neighbours.  Per site the arithmetic is that of
-// k_step_generic (same operations in the same order), so the fields agree bit
-// for bit; the block sums are added in another order.
+// The 1D step for N a multiple of VX = 16 / sizeof(T): each thread takes
+// groups of VX consecutive sites (step1d_group: 16-byte loads and stores, the
+// outer neighbours by scalar loads that hit L1, each site's g formed once per
+// field).  Per site the arithmetic is that of k_step_generic (same operations
+// in the same order), so the fields agree bit for bit; the block sums are
+// added in another order.
 template <typename T, int NF>
 __global__ void __launch_bounds__(kGenericThreads) k_step_1d(const StepArgs<T> p) {
   constexpr int VX = 16 / sizeof(T);
   const T c = (T)p.sc_in->c;
   const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
   const int64_t N = p.N, groups = N / VX;
-  T q[3] = {p.q[0], p.q[1], p.q[2]};
-  double grad2 = 0.0, pot = 0.0;   // flushed from the T partials every 4 groups
-  T g2loc = T(0), vloc = T(0);
+  const T q[3] = {p.q[0], p.q[1], p.q[2]};
+  T g2acc = T(0), vacc = T(0), g2loc = T(0), vloc = T(0);   // two-level sums in T (k_step_generic)
   int since_flush = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < groups; k += stride) {
-    const int64_t s = k * VX;
-    const int64_t sl = (k == 0) ? N - 1 : s - 1;             // left neighbour of the first site
-    const int64_t sr = (k == groups - 1) ? 0 : s + VX;       // right neighbour of the last site
-    T g[NF][VX + 2], v[NF][VX];   // g[i][1 + j] at site s + j; [0] and [VX + 1] the outer neighbours
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      T f[VX], w[VX];
-      ldg16<T, VX>(p.f_in[i] + s, f);
-      ldg16<T, VX>(p.w_in[i] + s, w);
-#pragma unroll
-      for (int j = 0; j < VX; ++j) {
-        v[i][j] = fmaT(c, f[j], w[j]);
-        g[i][j + 1] = fmaT(dd, v[i][j], f[j]);
-      }
-      const T fl = __ldg(p.f_in[i] + sl), wl = __ldg(p.w_in[i] + sl);
-      const T fr = __ldg(p.f_in[i] + sr), wr = __ldg(p.w_in[i] + sr);
-      g[i][0] = fmaT(dd, fmaT(c, fl, wl), fl);
-      g[i][VX + 1] = fmaT(dd, fmaT(c, fr, wr), fr);
-    }
-    T wo[NF][VX], fo[NF][VX];
-#pragma unroll
-    for (int j = 0; j < VX; ++j) {
-      T gs[NF], lap[NF];
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        const T gc = g[i][j + 1], gp = g[i][j + 2], gm = g[i][j];
-        T acc = T(0);
-        acc += (gp + gm) - T(2) * gc;
-        const T df = gp - gc;
-        g2loc = fmaT(df, df, g2loc);
-        lap[i] = acc * idx2;
-        gs[i] = gc;
-      }
-      T dv[NF], vs;
-      model_dv<T, NF>(gs, q, dv, vs);
-      vloc += vs;
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        wo[i][j] = fmaT(kk, lap[i] - dv[i], v[i][j]);
-        fo[i][j] = gs[i];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      stcs16<T, VX>(p.w_out[i] + s, wo[i]);
-      stcs16<T, VX>(p.f_out[i] + s, fo[i]);
-    }
+    step1d_group<T, NF>(p.f_in, p.w_in, p.f_out, p.w_out, N, k, c, dd, kk, idx2, q, g2loc, vloc);
     since_flush += VX;
     if (since_flush >= 16) {
-      grad2 += (double)g2loc;
-      pot += (double)vloc;
+      g2acc += g2loc;
+      vacc += vloc;
       g2loc = T(0);
       vloc = T(0);
       since_flush = 0;
     }
   }
-  if (p.update_scalars) {
-    grad2 += (double)g2loc;
-    pot += (double)vloc;
-    finish_step_block(p, grad2, pot);
-  }
+  if (p.update_scalars) finish_step_block(p, (double)g2acc + (double)g2loc, (double)vacc + (double)vloc);
 }
 
 template <typename T, int NF>

@@ -150,6 +150,14 @@ cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2]
                           int prec, int device, int rows_hint, int stages_hint, int zchunks_hint);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
+// 3D plane-sweep kernel with plain loads (any N): grid of 32 x 8 site
+// columns and z-chunks of zlen planes.
+struct PlanesPlan {
+  int gx, gy, gz, zlen;
+};
+PlanesPlan planes_plan(int64_t N, int nf, int prec, int sms);
+template <typename T> cudaError_t launch_step_planes(const StepArgs<T>& a, const PlanesPlan& plan,
+                                                     cudaStream_t st);
 namespace sweep {
 cudaError_t launch_f32(int variant, const StepArgs<float>& a, const SweepMaps& m, dim3 grid, size_t smem,
                        cudaStream_t st);
@@ -188,6 +196,7 @@ struct ce_sim {
   int generic_blocks = 1;
   int diag_blocks_max = 8;     // grid cap of the diagnostics pass: 8 blocks per SM
   ce::SweepPlan plan{};
+  ce::PlanesPlan planes{};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
   bool graphs_ok = true;
   int64_t bytes = 0;

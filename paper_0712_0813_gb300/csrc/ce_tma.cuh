@@ -1,6 +1,7 @@
-// ce_tma.cuh -- inline-PTX wrappers for mbarriers and TMA tensor copies on
-// sm_103a (mbarrier.init/arrive/try_wait, cp.async.bulk.tensor.3d with
-// mbarrier completion), shared by the z-sweep and batched step kernels.
+// ce_tma.cuh -- inline-PTX wrappers for mbarriers, TMA tensor copies and
+// per-thread asynchronous copies on sm_103a (mbarrier.init/arrive/try_wait,
+// cp.async.bulk.tensor.3d with mbarrier completion, cp.async with commit and
+// wait groups), shared by the step kernels.
 #pragma once
 
 #include <cuda.h>
@@ -11,6 +12,29 @@ namespace ce {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Per-thread asynchronous global -> shared copies (no registers held while in
+// flight): 16 bytes through L2 only, or BYTES = 4 / 8 / 16 through L1 as well.
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_small(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "n"(BYTES)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most PENDING of this thread's committed groups are in flight.
+template <int PENDING>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

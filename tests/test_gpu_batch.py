@@ -3,9 +3,9 @@
 * Each member of a mixed 1D/2D/3D batch matches the FP64 oracle (<= 1e-11
   relative max error after 30 steps), including ragged row segments (N not a
   multiple of the segment), every 3D segment width (32, 16 and 8 lanes per
-  row), partial row groups, 1D lattices swept over several spans with a
-  partial last span, and lattices with and without expansion in the same
-  launch.
+  row), partial row groups, 1D lattices over several blocks of the 1D launch
+  with a partial last block, and lattices with and without expansion in the
+  same launch; a batch of 1D lattices only (no persistent launch) as well.
 * "The same alone and in the mix": a lattice advanced in a batch of one and
   inside the mix is bit-identical (its items and their summation order do not
   depend on the other members), in FP32 and FP64.
@@ -25,7 +25,7 @@ MIX = [
     (2, 100, 2, (1.2,), True, 0.05),
     (2, 256, 2, (5.0,), True, 0.02),
     (1, 4096, 2, (1.2,), True, 0.004),
-    (1, 2600, 2, (3.0,), True, 0.004),  # full spans swept + a partial last span
+    (1, 2600, 2, (3.0,), True, 0.004),  # full blocks + a partial last block
     (1, 36, 2, (40.0,), False, 0.02),
 ]
 
@@ -69,6 +69,29 @@ def test_batch_members_match_oracle_fp64(gpu_capi, orc):
             assert abs(sc.a - ref.scale.a) <= 1e-11 * ref.scale.a
         en, en_ref = sim.energy(), orc.energy(ref)
         assert en["E"] == pytest.approx(en_ref["E"], rel=1e-10)
+        sim.close()
+
+
+def test_batch_of_1d_lattices_only_matches_oracle_fp64(gpu_capi, orc):
+    """A batch without 2D/3D members runs the 1D launch alone."""
+    capi = gpu_capi
+    cases = [c for c in MIX if c[0] == 1]
+    sims, inputs = [], []
+    for k, case in enumerate(cases):
+        sim, f0, u0 = make_sim(capi, case, "f64", 300 + k)
+        sims.append(sim)
+        inputs.append((f0, u0))
+    with capi.Batch(sims) as b:
+        b.step(40)
+        b.synchronize()
+    for k, (case, sim) in enumerate(zip(cases, sims)):
+        dims, N, nf, q, expansion, dt = case
+        p = orc.Params(dims=dims, N=N, L=20.0, dt=dt, nf=nf, q=q, expansion=expansion)
+        ref = orc.step(orc.init(p, *inputs[k]), 40)
+        f, v, sc = sim.get_fields(capi.CE_VEL_STAGGERED)
+        assert relmax(f, ref.f) <= 1e-11 and relmax(v, ref.v) <= 1e-11, case
+        if expansion:
+            assert abs(sc.a - ref.scale.a) <= 1e-11 * ref.scale.a
         sim.close()
 
 

@@ -405,14 +405,17 @@ def test_1d_kernel_vs_oracle(gpu_capi, orc, N, nf, precision):
 def auto_kernel(capi, dims, N, precision):
     """The kernel ce_create picks by itself (no plan hints).  FP32: the z-sweep
     kernel for 3D sides that are multiples of its tile, the row kernel for other
-    2D/3D lattices it takes with sides >= 64 (3D) or 512 (2D), the generic kernel
-    for the rest.  FP64: the generic kernel (its two-pass form in 2D/3D)."""
+    2D/3D lattices it takes with sides >= 64 (3D) or 512 (2D), the plane-sweep
+    kernel for the other 3D lattices, the generic kernel for the rest.  FP64:
+    the generic kernel (its two-pass form in 2D/3D)."""
     if precision == "f64":
         return capi.CE_KERNEL_GENERIC
     if dims == 3 and N % 128 == 0:
         return capi.CE_KERNEL_SWEEP
     if dims >= 2 and N % 4 == 0 and N >= (64 if dims == 3 else 512):
         return capi.CE_KERNEL_ROWS
+    if dims == 3:
+        return capi.CE_KERNEL_PLANES
     return capi.CE_KERNEL_GENERIC
 
 
@@ -433,3 +436,46 @@ def test_row_kernel_single_lattice(gpu_capi, orc, dims, N, precision):
         assert per_field_err(v, ref.v, nf) <= tol_v
     with gpu_capi.Simulation(dims=dims, N=N, L=20.0, dt=dt, nfields=nf, q=q, precision=precision) as auto:
         assert auto.kernel == auto_kernel(gpu_capi, dims, N, precision)
+
+
+# N, nf, q, dt: every neighbour wraps (3), a 1-site-wide last x tile and a
+# 1-row last row group (33), ragged tiles in x, y and z (37, 45)
+PLANES_CASES = [(3, 2, (1.2,), 0.05), (5, 1, (), 0.05), (33, 2, (1.2,), 0.05), (37, 3, (0.8, 5.0), 0.05),
+                (45, 4, (0.8, 5.0, 40.0), 0.02)]
+
+
+@pytest.mark.parametrize("N,nf,q,dt", PLANES_CASES, ids=[f"N{c[0]}_nf{c[1]}" for c in PLANES_CASES])
+def test_planes_kernel_fp64_vs_oracle(gpu_capi, orc, N, nf, q, dt):
+    """The 3D plane-sweep kernel (plain loads, any N) against the oracle over
+    100 steps with expansion, FP64."""
+    L = 20.0 if N > 5 else 3.0
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, 3, N, L, dt, nf, q, True, 100, kernel="planes", amp=1e-2)
+    with sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_PLANES
+        assert per_field_err(f, ref.f, nf) <= TOL64
+        assert per_field_err(v, ref.v, nf) <= TOL64
+        assert abs(sc.a - ref.scale.a) / ref.scale.a <= TOL64
+        assert abs(sc.ap_half - ref.scale.ap) / abs(ref.scale.ap) <= TOL64
+
+
+@pytest.mark.parametrize("N", [3, 33, 37, 61, 101])
+def test_planes_kernel_fields_equal_generic_fp32(gpu_capi, N):
+    """Per site the plane-sweep kernel does the generic kernel's arithmetic:
+    without expansion (no global sums feed back) the FP32 fields agree bit for
+    bit over many steps; with expansion they agree bit for bit after one step
+    (later steps differ only through the order of the global sums), and the
+    automatic FP32 choice for these sides is the plane-sweep kernel."""
+    nf, q = 2, (1.2,)
+    f0, u0 = lattice_ics(3, N, 20.0, nf, q=q, seed=4, amp=1e-2)
+    for expansion, steps in ((False, 20), (True, 1)):
+        out = []
+        for kernel in ("auto", "generic"):
+            with gpu_capi.Simulation(dims=3, N=N, L=20.0, dt=0.02, nfields=nf, q=q, expansion=expansion,
+                                     precision="f32", kernel=kernel) as sim:
+                assert sim.kernel == (gpu_capi.CE_KERNEL_PLANES if kernel == "auto" else gpu_capi.CE_KERNEL_GENERIC)
+                sim.set_fields(f0, u0)
+                sim.step(steps)
+                out.append(sim.get_fields(gpu_capi.CE_VEL_STAGGERED))
+        (fa, va, sa), (fb, vb, sb) = out
+        assert np.array_equal(fa, fb) and np.array_equal(va, vb), (N, expansion)
+        assert abs(sa.a - sb.a) <= 1e-15 * sb.a
