@@ -12,9 +12,10 @@
 // Block: 10 warps.  Warps 1..8 own the tile rows y0 .. y0 + 7 (lane = x - x0);
 // warp 0 computes the y-halo row y0 - 1 and warp 9 the row after the last
 // tile row (both mod N), so every g in the staged plane is computed once by
-// one thread.  In the tile warps, lane 0 also computes the x-halo site x0 - 1
-// and lane nx (lane 31 when the tile is 32 wide) the site x0 + nx (mod N),
-// where nx is the tile's width.
+// one thread.  Warp 0 also computes the x-halo sites: lane l < 16 the site
+// x0 - 1 of tile row l, lane 16 + l the site x0 + nx of tile row l (mod N; nx
+// is the tile's width), which keeps the tile warps' instruction stream free
+// of halo work.
 //
 // Loads: every thread copies the f and w values it needs (its own site, and
 // its x-halo site) with 4- or 8-byte cp.async into a shared-memory ring
@@ -66,14 +67,14 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
   const auto wrap = [&](int64_t v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
   const int64_t yrow = wrap((int64_t)y0 - 1 + r);
   const int64_t own = yrow * N + x0 + lane;                 // offset inside a plane
-  // x-halo site of this lane (tile warps only): lane 0 the left one (column 0),
-  // lane nx (an idle lane; lane 31 when nx = 32) the right one (column nx + 1)
-  const bool hleft = warp >= 1 && warp <= ny && lane == 0;
-  const bool hright = warp >= 1 && warp <= ny && lane == (nx < 32 ? nx : 31);
-  const bool halo = hleft || hright;
-  const int hcol = hleft ? 0 : nx + 1;
-  const int64_t hoff = yrow * N + (hleft ? wrap((int64_t)x0 - 1) : wrap((int64_t)x0 + nx));
-  const int cell = r * kPlaneCols + lane + 1, hcell = r * kPlaneCols + hcol;
+  // x-halo site of this lane (warp 0 only): staged row hr = 1 + (lane mod 16),
+  // column 0 (x0 - 1) for lanes 0..15, column nx + 1 (x0 + nx) for lanes 16..31
+  static_assert(kPlaneRows <= 16, "warp 0 holds one x-halo site per tile row and side");
+  const int hr = 1 + (lane & 15);
+  const bool halo = warp == 0 && hr <= ny;
+  const int hcol = lane < 16 ? 0 : nx + 1;
+  const int64_t hoff = wrap((int64_t)y0 - 1 + hr) * N + (lane < 16 ? wrap((int64_t)x0 - 1) : wrap((int64_t)x0 + nx));
+  const int cell = r * kPlaneCols + lane + 1, hcell = hr * kPlaneCols + hcol;
 
   const T c = (T)p.sc_in->c;
   const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
