@@ -188,8 +188,24 @@ def tune_budget(N: int) -> dict:
     return dict(steps=40, warmup=8, repeats=2)
 
 
+def lattice_stats(sim) -> dict:
+    en = sim.energy()
+    mean, var = sim.means_variances()
+    return {"step": int(en["step"]), "mean": [float(x) for x in mean], "var": [float(x) for x in var],
+            "E": float(en["E"]), "a": float(en["a"]), "ap": float(en["ap"])}
+
+
+def stats_error(got: dict, ref: dict) -> dict:
+    """Relative errors of lattice statistics (a mean against the field's spread)."""
+    spread = np.maximum(np.abs(np.asarray(ref["mean"])), np.sqrt(np.asarray(ref["var"])))
+    return {"mean": [float(x) for x in np.abs(np.asarray(got["mean"]) - np.asarray(ref["mean"])) / spread],
+            "var": [float(x) for x in np.abs(np.asarray(got["var"]) / np.asarray(ref["var"]) - 1.0)],
+            "E": abs(got["E"] / ref["E"] - 1.0), "a": abs(got["a"] / ref["a"] - 1.0),
+            "ap": abs(got["ap"] / ref["ap"] - 1.0) if ref["ap"] else None}
+
+
 def time_device_steps(capi, torch, w, f0, u0, precision, steps, warmup, barrier, sampler_gpu=None,
-                      hints=None, tune=False):
+                      hints=None, tune=False, stats=False):
     """Device-resident timing: CUDA events on the library's stream around
     `steps` launches.  With tune=True the z-sweep plan is autotuned on this
     same handle first (ce_replan between candidates; outside the timed
@@ -234,7 +250,10 @@ def time_device_steps(capi, torch, w, f0, u0, precision, steps, warmup, barrier,
     ms = e0.elapsed_time(e1)
     kernel = {1: "generic", 2: "sweep", 3: "rows", 4: "planes"}[sim.kernel]
     plan = sim.sweep_plan
+    st = lattice_stats(sim) if stats else None
     sim.close()
+    if stats:
+        return ms, kernel, clocks, plan, tune_info, st
     return ms, kernel, clocks, plan, tune_info
 
 
@@ -292,16 +311,16 @@ def cube256_leg(capi, torch, steps: int, warmup: int, hbm_peak: float, peak_kind
             "roofline": roofline_of(w, "f32", ms / steps, hbm_peak, peak_kind, kernel)}
 
 
-def fp32_error_leg(capi, torch):
+def fp32_error_leg(capi, torch, golden_path: str = GOLDEN_256):
     """FP32 (and FP64) outputs of the expanding 256^3 run against the oracle's
     stored values of the same run (tests/golden/longrun_256cube.json, written
     by the serial FP64 oracle only): f and f'(t+dt/2) at the stored sample of
     sites after 100 steps (max |gpu - oracle| / max over the lattice of
     |oracle|, per field), and means, variances, E, a, a' at every stored
     checkpoint up to 5000 steps (relative; a mean against the field's spread)."""
-    if not os.path.exists(GOLDEN_256):
-        return {"unavailable": "tests/golden/longrun_256cube.json is missing"}
-    with open(GOLDEN_256) as fh:
+    if not os.path.exists(golden_path):
+        return {"unavailable": f"{os.path.relpath(golden_path, ROOT)} is missing"}
+    with open(golden_path) as fh:
         gold = json.load(fh)
     c = gold["config"]
     w = dict(WORKLOADS["256cube"])
@@ -320,8 +339,7 @@ def fp32_error_leg(capi, torch):
         for cp in gold["checkpoints"]:
             sim.step(cp["step"] - done)
             done = cp["step"]
-            en = sim.energy()
-            mean, var = sim.means_variances()
+            got = lattice_stats(sim)
             if cp["step"] == gold["sample_step"] and "samples" in gold:
                 f, v, _ = sim.sample_fields(sites)
                 smp = gold["samples"]
@@ -329,12 +347,7 @@ def fp32_error_leg(capi, torch):
                                            for i in range(w["nf"])]
                 res["v_relmax_step100"] = [float(np.abs(v[i] - np.asarray(smp["v_staggered"][i])).max()
                                                  / smp["v_absmax"][i]) for i in range(w["nf"])]
-            spread = np.maximum(np.abs(np.asarray(cp["mean"])), np.sqrt(np.asarray(cp["var"])))
-            e = {"step": cp["step"],
-                 "mean": [float(x) for x in np.abs(mean - np.asarray(cp["mean"])) / spread],
-                 "var": [float(x) for x in np.abs(var / np.asarray(cp["var"]) - 1.0)],
-                 "E": abs(en["E"] / cp["E"] - 1.0), "a": abs(en["a"] / cp["a"] - 1.0),
-                 "ap": abs(en["ap"] / cp["ap"] - 1.0) if cp["ap"] else None}
+            e = dict(step=cp["step"], **stats_error(got, cp))
             res["checkpoints"].append(e)
             for k in ("mean", "var"):
                 worst[k] = max(worst.get(k, 0.0), max(e[k]))
@@ -639,6 +652,8 @@ def main():
     ap.add_argument("--cube256-steps", type=int, default=2000,
                     help="timed steps of the 256^3 leg (0: skip; skipped when it is the workload)")
     ap.add_argument("--no-fp32-error", action="store_true", help="skip the 256^3 errors against the oracle")
+    ap.add_argument("--golden", default=GOLDEN_256,
+                    help="stored oracle values of the 256^3 run for the fp32_error key")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU seconds per oracle leg")
@@ -733,10 +748,23 @@ def main():
                "job": f"set_fields(host f,u) + {args.steps} steps + get_fields(host f,u), pinned host buffers"}
 
     # plain FP64 path on the same lattice: the library's automatic FP64 choice
-    ms64, kernel64, _, plan64, _ = time_device_steps(capi, torch, w, f0, u0, "f64", args.fp64_steps,
-                                                     min(args.warmup, 5), barrier)
+    w64 = min(args.warmup, 5)
+    ms64, kernel64, _, plan64, _, st64 = time_device_steps(capi, torch, w, f0, u0, "f64", args.fp64_steps, w64,
+                                                           barrier, stats=True)
     ms64 = max_over_ranks(ms64)
     value64 = ws * S * args.fp64_steps / (ms64 / 1e3) / 1e9
+    # the headline lattice in FP32 (the timed launch plan) after the same number of
+    # steps, against the FP64 path (which matches the oracle to 1e-11 over 100
+    # steps on the lattices the oracle can run)
+    fp32_vs_fp64 = None
+    if rank == 0:
+        stream = torch.cuda.Stream()
+        with capi.Simulation(**sim_config(w, "f32", stream.cuda_stream, hints)) as sim32:
+            sim32.set_fields(f0, u0)
+            sim32.step(st64["step"])
+            st32 = lattice_stats(sim32)
+        fp32_vs_fp64 = {"steps": st64["step"], "errors": stats_error(st32, st64), "fp64": st64,
+                        "note": "FP32 storage against the FP64 path of the library on the same inputs"}
     del f0, u0
 
     cube256 = None
@@ -745,7 +773,7 @@ def main():
 
     fp32_error = None
     if not args.no_fp32_error and rank == 0:
-        fp32_error = fp32_error_leg(capi, torch)
+        fp32_error = fp32_error_leg(capi, torch, args.golden)
 
     batch = None
     if not args.no_batch:
@@ -778,6 +806,7 @@ def main():
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                            "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
             "roofline": roofline,
+            "fp32_vs_fp64": fp32_vs_fp64,
             "cube256": cube256,
             "fp32_error": fp32_error,
             "batched_mix": batch,
