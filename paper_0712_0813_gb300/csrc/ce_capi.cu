@@ -228,21 +228,73 @@ int fetch_aux(ce_sim* s, ce::DevAux* host) {
   return CE_OK;
 }
 
+// Host <-> device transfers through the staging buffer, pipelined: the buffer
+// is used as two halves; the handle's stream converts (or computes) one half
+// while the transfer stream copies the other, ordered by events (xready[b]:
+// half b holds data for its consumer; xfree[b]: its consumer is done with it),
+// with one host synchronisation per call instead of one per chunk.  Copies then
+// run back to back at the link's bandwidth.
+
+// Sites per half for `rows` values per site.
+int64_t half_sites(const ce_sim* s, int rows) {
+  return std::max<int64_t>(1, s->chunk * s->nf / (2 * rows));
+}
+
 // Host float64 -> device state array (one field).
 int upload_field(ce_sim* s, const double* src, void* dst) {
   if (s->prec == CE_F64) {
     cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)s->S * 8, cudaMemcpyHostToDevice, s->stream);
     return e == cudaSuccess ? CE_OK : cuda_fail(e, "H2D copy");
   }
-  for (int64_t s0 = 0; s0 < s->S; s0 += s->chunk) {
-    const int64_t n = std::min<int64_t>(s->chunk, s->S - s0);
-    cudaError_t e = cudaMemcpyAsync(s->staging, src + s0, (size_t)n * 8, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = ce::launch_from_f64<float>(s->staging, static_cast<float*>(dst) + s0, n, s->stream);
-    // the staging buffer is reused by the next chunk: order the copy after the conversion
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "H2D conversion");
+  const int64_t half = half_sites(s, 1);
+  // the staging buffer may still be read by earlier work on the handle's stream
+  cudaError_t e = cudaEventRecord(s->xstart, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->xfer, s->xstart, 0);
+  int k = 0;
+  for (int64_t s0 = 0; s0 < s->S && e == cudaSuccess; s0 += half, ++k) {
+    const int64_t n = std::min<int64_t>(half, s->S - s0);
+    const int b = k & 1;
+    double* buf = s->staging + (int64_t)b * half;
+    if (k >= 2) e = cudaStreamWaitEvent(s->xfer, s->xfree[b], 0);   // chunk k - 2 converted
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf, src + s0, (size_t)n * 8, cudaMemcpyHostToDevice, s->xfer);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xready[b], s->xfer);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->xready[b], 0);
+    if (e == cudaSuccess) e = ce::launch_from_f64<float>(buf, static_cast<float*>(dst) + s0, n, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xfree[b], s->stream);
+  }
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s->xfer);   // no copy may still read the caller's buffer after the return
+    return cuda_fail(e, "H2D conversion");
   }
   return CE_OK;
+}
+
+// Pipelined download of the handle's S sites, `rows` values per site:
+// produce(s0, n, buf) launches on the handle's stream the kernel that writes
+// rows x n doubles (row-major) for sites s0 .. s0 + n - 1 into buf; row r goes
+// to dst + r * S + s0.  Returns after every copy has landed in host memory.
+template <typename Produce>
+int pipelined_download(ce_sim* s, int rows, double* dst, Produce produce, const char* what) {
+  const int64_t half = half_sites(s, rows);
+  cudaError_t e = cudaSuccess;
+  int k = 0;
+  for (int64_t s0 = 0; s0 < s->S && e == cudaSuccess; s0 += half, ++k) {
+    const int64_t n = std::min<int64_t>(half, s->S - s0);
+    const int b = k & 1;
+    double* buf = s->staging + (int64_t)b * half * rows;
+    if (k >= 2) e = cudaStreamWaitEvent(s->stream, s->xfree[b], 0);   // chunk k - 2 copied out
+    if (e == cudaSuccess) e = produce(s0, n, buf);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xready[b], s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->xfer, s->xready[b], 0);
+    for (int r = 0; r < rows && e == cudaSuccess; ++r)
+      e = cudaMemcpyAsync(dst + (int64_t)r * s->S + s0, buf + (int64_t)r * n, (size_t)n * 8, cudaMemcpyDeviceToHost,
+                          s->xfer);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xfree[b], s->xfer);
+  }
+  const cudaError_t ex = cudaStreamSynchronize(s->xfer);   // every copy has landed (or failed)
+  if (e == cudaSuccess) e = ex;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? CE_OK : cuda_fail(e, what);
 }
 
 // Device state array (one field) -> host float64.  With w given, exports
@@ -253,22 +305,17 @@ int download_field(ce_sim* s, const void* f, const void* w, double* dst) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? CE_OK : cuda_fail(e, "D2H copy");
   }
-  for (int64_t s0 = 0; s0 < s->S; s0 += s->chunk) {
-    const int64_t n = std::min<int64_t>(s->chunk, s->S - s0);
-    cudaError_t e;
+  return pipelined_download(s, 1, dst, [&](int64_t s0, int64_t n, double* buf) -> cudaError_t {
     if (s->prec == CE_F32) {
       const float* fp = static_cast<const float*>(f) + s0;
-      e = w ? ce::launch_vhalf_to_f64<float>(fp, static_cast<const float*>(w) + s0, &s->aux->slot[s->cur], s->staging, n, s->stream)
-            : ce::launch_to_f64<float>(fp, s->staging, n, s->stream);
-    } else {
-      const double* fp = static_cast<const double*>(f) + s0;
-      e = ce::launch_vhalf_to_f64<double>(fp, static_cast<const double*>(w) + s0, &s->aux->slot[s->cur], s->staging, n, s->stream);
+      return w ? ce::launch_vhalf_to_f64<float>(fp, static_cast<const float*>(w) + s0, &s->aux->slot[s->cur], buf,
+                                                n, s->stream)
+               : ce::launch_to_f64<float>(fp, buf, n, s->stream);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst + s0, s->staging, (size_t)n * 8, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "D2H conversion");
-  }
-  return CE_OK;
+    const double* fp = static_cast<const double*>(f) + s0;
+    return ce::launch_vhalf_to_f64<double>(fp, static_cast<const double*>(w) + s0, &s->aux->slot[s->cur], buf, n,
+                                           s->stream);
+  }, "D2H conversion");
 }
 
 int check_sim(const ce_sim* s, const char* fn) {
@@ -400,6 +447,16 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
     ce_free(s);
     return fail(CE_ENOMEM, "ce_create: device allocation of scratch failed");
   }
+  e = cudaStreamCreateWithFlags(&s->xfer, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&s->xready[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->xfree[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->xstart, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    ce_free(s);
+    return cuda_fail(e, "ce_create: transfer stream");
+  }
   if (s->kernel == CE_KERNEL_ROWS) {
     rc = ce::rows_create(s, &s->rows);
     if (rc != CE_OK) {
@@ -431,7 +488,14 @@ void ce_free(ce_sim* s) {
     if (g) cudaGraphExecDestroy(g);
   ce::outputs_release(s);
   ce::rows_free(s->rows);
+  if (s->xfer) cudaStreamSynchronize(s->xfer);
   release_all(s);
+  if (s->xfer) cudaStreamDestroy(s->xfer);
+  for (int b = 0; b < 2; ++b) {
+    if (s->xready[b]) cudaEventDestroy(s->xready[b]);
+    if (s->xfree[b]) cudaEventDestroy(s->xfree[b]);
+  }
+  if (s->xstart) cudaEventDestroy(s->xstart);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -590,24 +654,17 @@ int ce_get_fields(ce_sim* s, double* f, double* v, int mode, ce_scalars_t* sc) {
     for (int i = 0; i < s->nf; ++i)
       if ((rc = download_field(s, s->f[s->cur][i], s->w[s->cur][i], v + (int64_t)i * s->S))) return rc;
   } else {
-    for (int64_t s0 = 0; s0 < s->S; s0 += s->chunk) {
-      const int64_t n = std::min<int64_t>(s->chunk, s->S - s0);
-      cudaError_t e;
+    rc = pipelined_download(s, s->nf, v, [&](int64_t s0, int64_t n, double* buf) -> cudaError_t {
       if (s->prec == CE_F32) {
         ce::DiagArgs<float> a = make_diag_args<float>(s, 0);
-        a.u_out = s->staging; a.s0 = s0; a.count = n;
-        e = ce::launch_sync_u_range<float>(a, s->stream);
-      } else {
-        ce::DiagArgs<double> a = make_diag_args<double>(s, 0);
-        a.u_out = s->staging; a.s0 = s0; a.count = n;
-        e = ce::launch_sync_u_range<double>(a, s->stream);
+        a.u_out = buf; a.s0 = s0; a.count = n;
+        return ce::launch_sync_u_range<float>(a, s->stream);
       }
-      for (int i = 0; i < s->nf && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(v + (int64_t)i * s->S + s0, s->staging + (int64_t)i * n, (size_t)n * 8,
-                            cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "ce_get_fields: synchronised velocity");
-    }
+      ce::DiagArgs<double> a = make_diag_args<double>(s, 0);
+      a.u_out = buf; a.s0 = s0; a.count = n;
+      return ce::launch_sync_u_range<double>(a, s->stream);
+    }, "ce_get_fields: synchronised velocity");
+    if (rc) return rc;
   }
   ce::DevAux host{};
   if ((rc = fetch_aux(s, &host))) return rc;

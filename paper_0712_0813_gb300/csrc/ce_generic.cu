@@ -322,7 +322,9 @@ template cudaError_t launch_step_generic<double>(const StepArgs<double>&, int, c
 // sites as in the step kernels: for FP32 storage the inputs carry 2^-24
 // relative rounding already, and FP64 per-site arithmetic (one conversion per
 // neighbour load) made the pass bound by GB300's FP64 rate.  The synchronised
-// velocity download (k_sync_u_range) keeps C = double.
+// velocity download (k_sync_u_range) uses C = the storage type as well (its
+// FP64 form made the download of a 1024^3 FP32 lattice FP64-bound: 0.32 s
+// against 0.20 s for the staggered velocity) and converts the result.
 template <typename T, typename C, int NF, int DIMS>
 __device__ __forceinline__ void site_u(const DiagArgs<T>& p, int64_t s, const SiteWalk<DIMS>& at,
                                        C (&fv)[NF], C (&u)[NF], C (&g2)[NF], C& vsite) {
@@ -482,10 +484,10 @@ __global__ void __launch_bounds__(256) k_sync_u_range(const DiagArgs<T> p) {
   at.init(p.s0 + k0, stride, p.N);
   for (int64_t k = k0; k < p.count; k += stride, at.advance(p.N)) {
     const int64_t s = p.s0 + k;
-    double fv[NF], u[NF], g2[NF], vs;
-    site_u<T, double, NF, DIMS>(p, s, at, fv, u, g2, vs);
+    T fv[NF], u[NF], g2[NF], vs;
+    site_u<T, T, NF, DIMS>(p, s, at, fv, u, g2, vs);
 #pragma unroll
-    for (int i = 0; i < NF; ++i) p.u_out[(int64_t)i * p.count + k] = u[i];
+    for (int i = 0; i < NF; ++i) p.u_out[(int64_t)i * p.count + k] = (double)u[i];
   }
 }
 

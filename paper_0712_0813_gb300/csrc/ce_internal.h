@@ -185,8 +185,10 @@ struct ce_sim {
   void* w[2][4] = {};
   ce::DevAux* aux = nullptr;
   double* partials = nullptr;
-  double* staging = nullptr;
+  double* staging = nullptr;    // chunk x nf doubles, used as two halves by the transfers
   int64_t chunk = 0;
+  cudaStream_t xfer = nullptr;  // host <-> device copies of the pipelined transfers
+  cudaEvent_t xready[2] = {nullptr, nullptr}, xfree[2] = {nullptr, nullptr}, xstart = nullptr;
   int cur = 0;
   bool have_state = false;
   double t = 0.0;
