@@ -36,7 +36,7 @@ import numpy as np
 import pytest
 
 from paper_0712_0813_gb300.icgen import courant_dt, lattice_ics
-from step_bounds import check_one_step
+from step_bounds import EPS64, check_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -162,3 +162,33 @@ def test_mixed_batch_sampled_step(gpu_capi, orc):
                        expansion=sp["expansion"])
         check_one_step(orc, local, p, before, after, sites, stencil, G, V)
         s.close()
+
+
+def test_full_size_1024cube_fp64_sampled_step(gpu_capi, orc):
+    """The bench's FP64 leg: 3D 1024^3, 2 fields, expansion, FP64 storage (68.7 GB)
+    on the automatic FP64 choice (the generic kernel's two passes), one step
+    checked at sampled sites against the oracle's per-site step, with the G and
+    V of the drifted fields summed by the oracle over the whole lattice; bounds
+    of one step in FP64 (EPS64), a'' to 1e-10 of its source term."""
+    import torch
+    from oracle import local
+    capi = gpu_capi
+    N, nf, q, L = 1024, 2, (1.2,), 20.0
+    dt = courant_dt(3, N, L, 1.0, q)
+    p = orc.Params(dims=3, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
+    f0, u0 = lattice_ics(3, N, L, nf, q=q, seed=1, backend="torch")
+    torch.cuda.empty_cache()
+    with capi.Simulation(dims=3, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision="f64") as sim:
+        assert sim.kernel == capi.CE_KERNEL_GENERIC
+        sim.set_fields(f0, u0)
+        del f0, u0
+        gc.collect()
+        sim.step(3)
+        sites = plan_sites(N, 64, 8, 4)
+        stencil = local.stencil_sites(3, N, sites)
+        before = sim.sample_fields(stencil)
+        G, V = oracle_sums(local, p, sim)
+        sim.step(1)
+        after = sim.sample_fields(sites)
+    check_one_step(orc, local, p, before, after, sites, stencil, G, V, eps=EPS64, sums_rel=1e-10)
+    assert after[2].step == 4
