@@ -70,7 +70,7 @@ extern "C" {
 
 /* ---- kernel selection (ce_config.kernel) ------------------------------ */
 #define CE_KERNEL_AUTO    0 /* FP32: z-sweep kernel where it applies; else the
-                               row kernel for 2D sides >= 512 and 3D sides >= 64
+                               row kernel for 2D sides >= 512 and 3D sides >= 96
                                it takes; else, in 3D, the plane-sweep kernel;
                                else generic.  FP64: generic (its two-pass
                                form), or the z-sweep kernel when plan hints

@@ -32,9 +32,10 @@ constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
 // Smallest sides for which the automatic choice takes the row kernel (FP32),
-// from timings of both kernels on single lattices: below them a lattice is a
-// few microseconds of traffic and the generic kernel starts faster.
-constexpr int kRowsMinN3 = 64;
+// from timings on single lattices: below them a lattice is a few microseconds
+// of traffic and the plane-sweep kernel (3D; 64^3: 13.1 against 15.8 us, 96^3:
+// 19.2 against 19.0) or the generic kernel (2D) starts faster.
+constexpr int kRowsMinN3 = 96;
 constexpr int kRowsMinN2 = 512;
 constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device-side wait

@@ -405,14 +405,14 @@ def test_1d_kernel_vs_oracle(gpu_capi, orc, N, nf, precision):
 def auto_kernel(capi, dims, N, precision):
     """The kernel ce_create picks by itself (no plan hints).  FP32: the z-sweep
     kernel for 3D sides that are multiples of its tile, the row kernel for other
-    2D/3D lattices it takes with sides >= 64 (3D) or 512 (2D), the plane-sweep
+    2D/3D lattices it takes with sides >= 96 (3D) or 512 (2D), the plane-sweep
     kernel for the other 3D lattices, the generic kernel for the rest.  FP64:
     the generic kernel (its two-pass form in 2D/3D)."""
     if precision == "f64":
         return capi.CE_KERNEL_GENERIC
     if dims == 3 and N % 128 == 0:
         return capi.CE_KERNEL_SWEEP
-    if dims >= 2 and N % 4 == 0 and N >= (64 if dims == 3 else 512):
+    if dims >= 2 and N % 4 == 0 and N >= (96 if dims == 3 else 512):
         return capi.CE_KERNEL_ROWS
     if dims == 3:
         return capi.CE_KERNEL_PLANES
