@@ -150,10 +150,10 @@ cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2]
                           int prec, int device, int rows_hint, int stages_hint, int zchunks_hint);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
-// 3D plane-sweep kernel with plain loads (any N): grid of 32 x 8 site
-// columns and z-chunks of zlen planes.
+// 3D plane-sweep kernel with plain loads (any N): grid of (32 sx) x 8 site
+// columns (sx sites per lane, 1 or 2) and z-chunks of zlen planes.
 struct PlanesPlan {
-  int gx, gy, gz, zlen;
+  int gx, gy, gz, zlen, sx;
 };
 PlanesPlan planes_plan(int64_t N, int nf, int prec, int sms);
 template <typename T> cudaError_t launch_step_planes(const StepArgs<T>& a, const PlanesPlan& plan,

@@ -1,4 +1,4 @@
-// ce_planes3d.cu -- the 3D step for any side N: a block owns a 32 x 8 column
+// ce_planes3d.cu -- the 3D step for any side N: a block owns a 64 x 8 column
 // of sites and sweeps a chunk of z-planes, with plain coalesced loads (no
 // alignment needed, so odd sides work), each site's drifted g formed once per
 // plane in shared memory, and z-neighbours carried in registers.
@@ -9,23 +9,28 @@
 // f_out = g), so the fields agree with k_step_generic bit for bit; only the
 // global sums are added in another order.
 //
-// Block: 10 warps.  Warps 1..8 own the tile rows y0 .. y0 + 7 (lane = x - x0);
-// warp 0 computes the y-halo row y0 - 1 and warp 9 the row after the last
-// tile row (both mod N), so every g in the staged plane is computed once by
-// one thread.  Warp 0 also computes the x-halo sites: lane l < 16 the site
-// x0 - 1 of tile row l, lane 16 + l the site x0 + nx of tile row l (mod N; nx
-// is the tile's width), which keeps the tile warps' instruction stream free
-// of halo work.
+// Block: 10 warps over a tile of 32 SX x 8 sites.  Warps 1..8 own the tile
+// rows y0 .. y0 + 7, lane l the sites x0 + l + 32 h, h < SX.  SX = 2 on large
+// lattices (from side 192: the per-plane costs -- offsets, the barrier, the
+// loop -- are shared by two sites, and the second site's loads and stores use
+// immediate offsets; 383^3: 432 -> 413 us), SX = 1 below (more blocks: 64^3
+// 13.1 against 16.8 us).  Warp 0
+// computes the y-halo row y0 - 1 and warp 9 the row after the last tile row
+// (both mod N), so every g in the staged plane is computed once by one thread.
+// Warp 0 also computes the x-halo sites: lane l < 16 the site x0 - 1 of tile
+// row l, lane 16 + l the site x0 + nx of tile row l (mod N; nx is the tile's
+// width), which keeps the tile warps' instruction stream free of halo work.
 //
-// Loads: every thread copies the f and w values it needs (its own site, and
+// Loads: every thread copies the f and w values it needs (its own sites, and
 // its x-halo site) with 4- or 8-byte cp.async into a shared-memory ring
-// kDepth planes deep, kDepth - 1 planes ahead of the plane it forms; only
-// the thread itself reads those slots, so the ring needs no barrier, and the
-// copies in flight hold no registers (the latency of HBM needs ~40 KB in
-// flight per SM).  A plane's g goes into one of three g buffers; the single
-// block barrier per plane publishes it, and three buffers make that one
-// barrier enough (a buffer is rewritten two planes after it was last read).
-// The z-chunk covers planes z0 .. z1 - 1 and stages z0 - 1 and z1 as well.
+// D planes deep, D - 1 planes ahead of the plane it forms (D = 4 for FP32 with
+// up to 2 fields; fewer where the ring would not fit); only the thread itself
+// reads those slots, so the ring needs no barrier, and the copies in flight
+// hold no registers (the latency of HBM needs ~40 KB in flight per SM).  A
+// plane's g goes into one of three g buffers; the single block barrier per
+// plane publishes it, and three buffers make that one barrier enough (a buffer
+// is rewritten two planes after it was last read).  The z-chunk covers planes
+// z0 .. z1 - 1 and stages z0 - 1 and z1 as well.
 #include <cstdint>
 
 #include "ce_device.cuh"
@@ -38,35 +43,54 @@ namespace {
 constexpr int kPlaneRows = 8;                 // tile rows per block
 constexpr int kPlaneWarps = kPlaneRows + 2;   // plus the two y-halo warps
 constexpr int kPlaneThreads = 32 * kPlaneWarps;
-constexpr int kPlaneCols = 34;                // x-halo, 32 tile columns, x-halo
-constexpr int kPlaneCells = (kPlaneRows + 2) * kPlaneCols;
-constexpr int kDepth = 4;                     // planes of f, w in the copy ring
+// staged columns: x-halo, the 32 SX tile columns, x-halo
+template <int SX>
+struct Tile {
+  static constexpr int X = 32 * SX;
+  static constexpr int cols = X + 2;
+  static constexpr int cells = (kPlaneRows + 2) * cols;
+};
+
+// planes of f, w in the copy ring: the ring and three g buffers fit the SM's
+// shared memory for every storage type and field count
+template <typename T, int NF>
+struct RingDepth {
+  static constexpr int value = sizeof(T) * NF <= 8 ? 4 : (sizeof(T) * NF <= 16 ? 3 : 2);
+};
 
 // dynamic shared memory: 3 g buffers of NF planes, then the copy ring
-template <typename T, int NF>
+template <typename T, int NF, int SX>
 constexpr size_t planes_smem() {
-  return sizeof(T) * (size_t)kPlaneCells * NF * (3 + 2 * kDepth);
+  return sizeof(T) * (size_t)Tile<SX>::cells * NF * (3 + 2 * RingDepth<T, NF>::value);
 }
 
-template <typename T, int NF>
+template <typename T, int NF, int SX>
 __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T> p, int zlen) {
+  constexpr int D = RingDepth<T, NF>::value;
+  constexpr int kTileX = Tile<SX>::X, kPlaneCols = Tile<SX>::cols, kPlaneCells = Tile<SX>::cells;
   extern __shared__ __align__(16) unsigned char planes_smem_dyn[];
   T* const sg = reinterpret_cast<T*>(planes_smem_dyn);             // [3][NF][rows + 2][cols]
-  T* const ring = sg + 3 * NF * kPlaneCells;                        // [kDepth][NF][f, w][rows + 2][cols]
+  T* const ring = sg + 3 * NF * kPlaneCells;                        // [D][NF][f, w][rows + 2][cols]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t N = p.N, NN = N * N;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kPlaneRows;
-  const int nx = (int)min((int64_t)32, N - x0), ny = (int)min((int64_t)kPlaneRows, N - y0);
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kPlaneRows;
+  const int nx = (int)min((int64_t)kTileX, N - x0), ny = (int)min((int64_t)kPlaneRows, N - y0);
   const int z0 = blockIdx.z * zlen;
   const int z1 = (int)min((int64_t)z0 + zlen, N);
   // staged row r of this warp: 0 = row y0 - 1, 1 .. ny = tile rows, ny + 1 = the row after them
   const int r = warp == kPlaneWarps - 1 ? ny + 1 : warp;
   const bool row_on = warp == 0 || warp == kPlaneWarps - 1 || warp <= ny;
-  const bool tile = warp >= 1 && warp <= ny && lane < nx;   // updates a site
-  const bool act = row_on && lane < nx;                     // forms a g each plane
+  const bool tile_row = warp >= 1 && warp <= ny;
+  // sites h < SX of this lane: x0 + lane + 32 h, inside the tile when < nx
+  bool act[SX], upd_site[SX];
+#pragma unroll
+  for (int h = 0; h < SX; ++h) {
+    act[h] = row_on && lane + 32 * h < nx;         // forms a g each plane
+    upd_site[h] = tile_row && lane + 32 * h < nx;  // updates the site
+  }
   const auto wrap = [&](int64_t v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
   const int64_t yrow = wrap((int64_t)y0 - 1 + r);
-  const int64_t own = yrow * N + x0 + lane;                 // offset inside a plane
+  const int64_t own = yrow * N + x0 + lane;                 // offset inside a plane of site 0
   // x-halo site of this lane (warp 0 only): staged row hr = 1 + (lane mod 16),
   // column 0 (x0 - 1) for lanes 0..15, column nx + 1 (x0 + nx) for lanes 16..31
   static_assert(kPlaneRows <= 16, "warp 0 holds one x-halo site per tile row and side");
@@ -74,7 +98,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
   const bool halo = warp == 0 && hr <= ny;
   const int hcol = lane < 16 ? 0 : nx + 1;
   const int64_t hoff = wrap((int64_t)y0 - 1 + hr) * N + (lane < 16 ? wrap((int64_t)x0 - 1) : wrap((int64_t)x0 + nx));
-  const int cell = r * kPlaneCols + lane + 1, hcell = hr * kPlaneCols + hcol;
+  const int cell = r * kPlaneCols + lane + 1, hcell = hr * kPlaneCols + hcol;   // site h: cell + 32 h
 
   const T c = (T)p.sc_in->c;
   const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
@@ -103,10 +127,12 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
       T* rs = ring + (size_t)slot * NF * 2 * kPlaneCells;
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
-        if (act) {
-          cp_small<sizeof(T)>(rs + (2 * i) * kPlaneCells + cell, fo[i] + zoff);
-          cp_small<sizeof(T)>(rs + (2 * i + 1) * kPlaneCells + cell, wo[i] + zoff);
-        }
+#pragma unroll
+        for (int h = 0; h < SX; ++h)
+          if (act[h]) {
+            cp_small<sizeof(T)>(rs + (2 * i) * kPlaneCells + cell + 32 * h, fo[i] + zoff + 32 * h);
+            cp_small<sizeof(T)>(rs + (2 * i + 1) * kPlaneCells + cell + 32 * h, wo[i] + zoff + 32 * h);
+          }
         if (halo) {
           cp_small<sizeof(T)>(rs + (2 * i) * kPlaneCells + hcell, fh[i] + zoff);
           cp_small<sizeof(T)>(rs + (2 * i + 1) * kPlaneCells + hcell, wh[i] + zoff);
@@ -118,76 +144,84 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
   };
 
   // three register sets: R[k] holds g (and v) of the staged planes j = k mod 3
-  T g0[NF], g1[NF], g2[NF], v0[NF], v1[NF], v2[NF];
+  T g0[NF][SX], g1[NF][SX], g2[NF][SX], v0[NF][SX], v1[NF][SX], v2[NF][SX];
 #pragma unroll
-  for (int i = 0; i < NF; ++i) g0[i] = g1[i] = g2[i] = v0[i] = v1[i] = v2[i] = T(0);
+  for (int i = 0; i < NF; ++i)
+#pragma unroll
+    for (int h = 0; h < SX; ++h) g0[i][h] = g1[i][h] = g2[i][h] = v0[i][h] = v1[i][h] = v2[i][h] = T(0);
   // two-level sums in T, converted to FP64 once per thread (see k_step_generic)
   T g2acc = T(0), vacc = T(0), g2loc = T(0), vloc = T(0);
   int since_flush = 0;
-  int64_t upd = (int64_t)z0 * NN + own;                     // output offset of the next updated site
+  int64_t upd = (int64_t)z0 * NN + own;                     // output offset of the next updated plane
 
-  // staged plane j: form its g from ring slot j mod kDepth into g buffer
-  // `form` (j mod 3) and gn, copy plane j + kDepth - 1 into its slot (that of
-  // plane j - 1, which this thread read in the previous stage), then (j >= 2)
-  // update plane j - 1 from g buffer `read` ((j - 1) mod 3)
-  // with z-neighbours gm (plane j - 2) and gn (plane j), own g gc and v vc
-  // (plane j - 1)
-  const auto stage = [&](int j, T* form, const T* read, T (&gn)[NF], T (&vn)[NF], const T (&gm)[NF],
-                         const T (&gc)[NF], const T (&vc)[NF]) {
-    cp_wait<kDepth - 2>();                                  // this thread's copies of plane j have landed
-    const int slot = j % kDepth;
-    const T* rs = ring + (size_t)slot * NF * 2 * kPlaneCells;
+  // staged plane j: form its g from ring slot j mod D into g buffer `form`
+  // (j mod 3) and gn, copy plane j + D - 1 into its slot (that of plane j - 1,
+  // which this thread read in the previous stage), then (j >= 2) update plane
+  // j - 1 from g buffer `read` ((j - 1) mod 3) with z-neighbours gm (plane
+  // j - 2) and gn (plane j), own g gc and v vc (plane j - 1)
+  const auto stage = [&](int j, T* form, const T* read, T (&gn)[NF][SX], T (&vn)[NF][SX], const T (&gm)[NF][SX],
+                         const T (&gc)[NF][SX], const T (&vc)[NF][SX]) {
+    cp_wait<D - 2>();                                       // this thread's copies of plane j have landed
+    const T* rs = ring + (size_t)(j % D) * NF * 2 * kPlaneCells;
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
-      if (act) {
-        const T f = rs[(2 * i) * kPlaneCells + cell], w = rs[(2 * i + 1) * kPlaneCells + cell];
-        vn[i] = fmaT(c, f, w);
-        gn[i] = fmaT(dd, vn[i], f);
-        form[i * kPlaneCells + cell] = gn[i];
-      }
+#pragma unroll
+      for (int h = 0; h < SX; ++h)
+        if (act[h]) {
+          const T f = rs[(2 * i) * kPlaneCells + cell + 32 * h], w = rs[(2 * i + 1) * kPlaneCells + cell + 32 * h];
+          vn[i][h] = fmaT(c, f, w);
+          gn[i][h] = fmaT(dd, vn[i][h], f);
+          form[i * kPlaneCells + cell + 32 * h] = gn[i][h];
+        }
       if (halo) {
         const T f = rs[(2 * i) * kPlaneCells + hcell], w = rs[(2 * i + 1) * kPlaneCells + hcell];
         form[i * kPlaneCells + hcell] = fmaT(dd, fmaT(c, f, w), f);
       }
     }
-    issue((j + kDepth - 1) % kDepth, j + kDepth - 1 < n);   // the slot of plane j - 1, read last stage
+    issue((j + D - 1) % D, j + D - 1 < n);                  // the slot of plane j - 1, read last stage
     __syncthreads();
-    if (j < 2 || !tile) return;
-    T lap[NF];
+    if (j < 2 || !tile_row) return;
 #pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      const T* rd = read + i * kPlaneCells + cell;
-      const T g = gc[i];
-      T acc = T(0);
-      {
-        const T xp = rd[1], xm = rd[-1];
-        acc += (xp + xm) - T(2) * g;
-        const T df = xp - g;
-        g2loc = fmaT(df, df, g2loc);
-      }
-      {
-        const T yp = rd[kPlaneCols], ym = rd[-kPlaneCols];
-        acc += (yp + ym) - T(2) * g;
-        const T df = yp - g;
-        g2loc = fmaT(df, df, g2loc);
-      }
-      {
-        acc += (gn[i] + gm[i]) - T(2) * g;
-        const T df = gn[i] - g;
-        g2loc = fmaT(df, df, g2loc);
-      }
-      lap[i] = acc * idx2;
-    }
-    T dv[NF], vs;
-    model_dv<T, NF>(gc, q, dv, vs);
-    vloc += vs;
+    for (int h = 0; h < SX; ++h) {
+      if (!upd_site[h]) continue;
+      T lap[NF], gs[NF];
 #pragma unroll
-    for (int i = 0; i < NF; ++i) {
-      __stcs(p.w_out[i] + upd, fmaT(kk, lap[i] - dv[i], vc[i]));
-      __stcs(p.f_out[i] + upd, gc[i]);
+      for (int i = 0; i < NF; ++i) {
+        const T* rd = read + i * kPlaneCells + cell + 32 * h;
+        const T g = gc[i][h];
+        T acc = T(0);
+        {
+          const T xp = rd[1], xm = rd[-1];
+          acc += (xp + xm) - T(2) * g;
+          const T df = xp - g;
+          g2loc = fmaT(df, df, g2loc);
+        }
+        {
+          const T yp = rd[kPlaneCols], ym = rd[-kPlaneCols];
+          acc += (yp + ym) - T(2) * g;
+          const T df = yp - g;
+          g2loc = fmaT(df, df, g2loc);
+        }
+        {
+          acc += (gn[i][h] + gm[i][h]) - T(2) * g;
+          const T df = gn[i][h] - g;
+          g2loc = fmaT(df, df, g2loc);
+        }
+        lap[i] = acc * idx2;
+        gs[i] = g;
+      }
+      T dv[NF], vs;
+      model_dv<T, NF>(gs, q, dv, vs);
+      vloc += vs;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        __stcs(p.w_out[i] + upd + 32 * h, fmaT(kk, lap[i] - dv[i], vc[i][h]));
+        __stcs(p.f_out[i] + upd + 32 * h, gs[i]);
+      }
+      ++since_flush;
     }
     upd += NN;   // the chunk's planes z0 .. z1 - 1 do not wrap
-    if (++since_flush == 16) {
+    if (since_flush >= 16) {
       g2acc += g2loc;
       vacc += vloc;
       g2loc = T(0);
@@ -196,7 +230,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
     }
   };
 #pragma unroll
-  for (int k = 0; k < kDepth - 1; ++k) issue(k, k < n);
+  for (int k = 0; k < D - 1; ++k) issue(k, k < n);
   T* const b0 = sg;
   T* const b1 = sg + NF * kPlaneCells;
   T* const b2 = sg + 2 * NF * kPlaneCells;
@@ -211,42 +245,50 @@ __global__ void __launch_bounds__(kPlaneThreads) k_step_planes(const StepArgs<T>
 
 template <typename T, int NF>
 cudaError_t launch_nf(const StepArgs<T>& a, const PlanesPlan& pl, cudaStream_t st) {
-  k_step_planes<T, NF><<<dim3(pl.gx, pl.gy, pl.gz), kPlaneThreads, planes_smem<T, NF>(), st>>>(a, pl.zlen);
+  if (pl.sx == 2)
+    k_step_planes<T, NF, 2><<<dim3(pl.gx, pl.gy, pl.gz), kPlaneThreads, planes_smem<T, NF, 2>(), st>>>(a, pl.zlen);
+  else
+    k_step_planes<T, NF, 1><<<dim3(pl.gx, pl.gy, pl.gz), kPlaneThreads, planes_smem<T, NF, 1>(), st>>>(a, pl.zlen);
   return cudaGetLastError();
 }
 
 // Raise the kernel's dynamic shared-memory limit (FP64 with 4 fields needs
-// ~120 KB) and report how many blocks fit an SM.
-template <typename T, int NF>
+// ~120 KB at SX = 1) and report how many blocks fit an SM.
+template <typename T, int NF, int SX>
 int blocks_per_sm() {
-  const void* k = (const void*)&k_step_planes<T, NF>;
+  const void* k = (const void*)&k_step_planes<T, NF, SX>;
   int n = 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)planes_smem<T, NF>()) !=
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)planes_smem<T, NF, SX>()) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kPlaneThreads, planes_smem<T, NF>()) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kPlaneThreads, planes_smem<T, NF, SX>()) !=
+          cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return n < 1 ? 1 : n;
 }
 
+template <typename T, int SX>
+int blocks_per_sm_nf(int nf) {
+  return nf == 1 ? blocks_per_sm<T, 1, SX>() : nf == 2 ? blocks_per_sm<T, 2, SX>()
+       : nf == 3 ? blocks_per_sm<T, 3, SX>() : blocks_per_sm<T, 4, SX>();
+}
+
+constexpr int64_t kTwoSitesMinN = 192;   // sides from which each lane takes two sites
+
 }  // namespace
 
-// Grid of the plane-sweep kernel: 32 x 8 columns of sites, z split into
+// Grid of the plane-sweep kernel: 32 SX x 8 columns of sites, z split into
 // chunks so that about two waves of resident blocks are busy, with chunks of
 // at least 8 planes (each chunk stages 2 halo planes besides its own).
 PlanesPlan planes_plan(int64_t N, int nf, int prec, int sms) {
   PlanesPlan pl{};
-  pl.gx = (int)((N + 31) / 32);
+  pl.sx = N >= kTwoSitesMinN ? 2 : 1;
+  pl.gx = (int)((N + 32 * pl.sx - 1) / (32 * pl.sx));
   pl.gy = (int)((N + kPlaneRows - 1) / kPlaneRows);
-  int per_sm = 1;
-  if (prec == CE_F32) {
-    per_sm = nf == 1 ? blocks_per_sm<float, 1>() : nf == 2 ? blocks_per_sm<float, 2>()
-           : nf == 3 ? blocks_per_sm<float, 3>() : blocks_per_sm<float, 4>();
-  } else {
-    per_sm = nf == 1 ? blocks_per_sm<double, 1>() : nf == 2 ? blocks_per_sm<double, 2>()
-           : nf == 3 ? blocks_per_sm<double, 3>() : blocks_per_sm<double, 4>();
-  }
+  int per_sm;
+  if (prec == CE_F32) per_sm = pl.sx == 2 ? blocks_per_sm_nf<float, 2>(nf) : blocks_per_sm_nf<float, 1>(nf);
+  else per_sm = pl.sx == 2 ? blocks_per_sm_nf<double, 2>(nf) : blocks_per_sm_nf<double, 1>(nf);
   const int64_t cols = (int64_t)pl.gx * pl.gy;
   const int64_t want = std::max<int64_t>(1, (2LL * per_sm * sms + cols - 1) / cols);
   const int64_t gz = std::max<int64_t>(1, std::min<int64_t>(want, N / 8));

@@ -438,18 +438,20 @@ def test_row_kernel_single_lattice(gpu_capi, orc, dims, N, precision):
         assert auto.kernel == auto_kernel(gpu_capi, dims, N, precision)
 
 
-# N, nf, q, dt: every neighbour wraps (3), a 1-site-wide last x tile and a
-# 1-row last row group (33), ragged tiles in x, y and z (37, 45)
-PLANES_CASES = [(3, 2, (1.2,), 0.05), (5, 1, (), 0.05), (33, 2, (1.2,), 0.05), (37, 3, (0.8, 5.0), 0.05),
-                (45, 4, (0.8, 5.0, 40.0), 0.02)]
+# N, nf, q, dt, steps: every neighbour wraps (3), a 1-site-wide last x tile and a
+# 1-row last row group (33), ragged tiles in x, y and z (37, 45); from side 192
+# each lane takes two sites (64-wide tiles): 195 leaves a 3-wide last tile
+PLANES_CASES = [(3, 2, (1.2,), 0.05, 100), (5, 1, (), 0.05, 100), (33, 2, (1.2,), 0.05, 100),
+                (37, 3, (0.8, 5.0), 0.05, 100), (45, 4, (0.8, 5.0, 40.0), 0.02, 100), (195, 2, (1.2,), 0.02, 6)]
 
 
-@pytest.mark.parametrize("N,nf,q,dt", PLANES_CASES, ids=[f"N{c[0]}_nf{c[1]}" for c in PLANES_CASES])
-def test_planes_kernel_fp64_vs_oracle(gpu_capi, orc, N, nf, q, dt):
-    """The 3D plane-sweep kernel (plain loads, any N) against the oracle over
-    100 steps with expansion, FP64."""
+@pytest.mark.parametrize("N,nf,q,dt,steps", PLANES_CASES, ids=[f"N{c[0]}_nf{c[1]}" for c in PLANES_CASES])
+def test_planes_kernel_fp64_vs_oracle(gpu_capi, orc, N, nf, q, dt, steps):
+    """The 3D plane-sweep kernel (plain loads, any N) against the oracle with
+    expansion, FP64 (100 steps; 6 on the 195^3 lattice, which the oracle
+    steps in about a second each)."""
     L = 20.0 if N > 5 else 3.0
-    ref, sim, f, v, sc = run_pair(orc, gpu_capi, 3, N, L, dt, nf, q, True, 100, kernel="planes", amp=1e-2)
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, 3, N, L, dt, nf, q, True, steps, kernel="planes", amp=1e-2)
     with sim:
         assert sim.kernel == gpu_capi.CE_KERNEL_PLANES
         assert per_field_err(f, ref.f, nf) <= TOL64
@@ -458,7 +460,7 @@ def test_planes_kernel_fp64_vs_oracle(gpu_capi, orc, N, nf, q, dt):
         assert abs(sc.ap_half - ref.scale.ap) / abs(ref.scale.ap) <= TOL64
 
 
-@pytest.mark.parametrize("N", [3, 33, 37, 61, 101])
+@pytest.mark.parametrize("N", [3, 33, 37, 61, 101, 197, 225])
 def test_planes_kernel_fields_equal_generic_fp32(gpu_capi, N):
     """Per site the plane-sweep kernel does the generic kernel's arithmetic:
     without expansion (no global sums feed back) the FP32 fields agree bit for
