@@ -538,8 +538,8 @@ def shapes_mode(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> i
       one k_step_batched launch per step, at two item lengths;
     * batch_3d: homogeneous batches of about 100 M sites of one 3D side;
     * single: one lattice stepped by ce_step with the generic kernel, the row
-      kernel (CE_KERNEL_ROWS, sides that are multiples of 4) and in 3D the
-      plane-sweep kernel (CE_KERNEL_PLANES), FP32 and FP64.
+      kernel (CE_KERNEL_ROWS, sides that are multiples of 4) and the plane /
+      line-sweep kernel (CE_KERNEL_PLANES, 3D / 2D), FP32 and FP64.
 
     CUDA events on the library's stream around `steps` steps after `warmup`;
     frac = the algorithmic 16 B per field and site / time / measured HBM."""
@@ -584,13 +584,13 @@ def shapes_mode(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> i
         print(json.dumps(row), flush=True)
         for sim in sims:
             sim.close()
-    for dims, N in ((1, 65536), (2, 1024), (2, 6000), (3, 48), (3, 64), (3, 95), (3, 96), (3, 160), (3, 192),
-                    (3, 255), (3, 288), (3, 383), (3, 448), (3, 511)):
+    for dims, N in ((1, 65536), (2, 1023), (2, 1024), (2, 6000), (2, 6001), (3, 48), (3, 64), (3, 95), (3, 96),
+                    (3, 160), (3, 192), (3, 255), (3, 288), (3, 383), (3, 448), (3, 511)):
         big = N ** dims >= 1 << 22
         f0, u0 = lattice_ics(dims, N, 20.0, 2, q=(1.2,), seed=3, amp=1e-2, backend="torch" if big else "numpy")
         dt = courant_dt(dims, N, 20.0, 1.0, (1.2,))
         row = {"case": "single", "dims": dims, "N": N}
-        kernels = ("generic",) + (("rows",) if N % 4 == 0 else ()) + (("planes",) if dims == 3 else ())
+        kernels = ("generic",) + (("rows",) if N % 4 == 0 else ()) + (("planes",) if dims >= 2 else ())
         for prec in ("f32", "f64"):
             for kern in kernels:
                 with capi.Simulation(dims=dims, N=N, L=20.0, dt=dt, nfields=2, q=(1.2,), expansion=True,

@@ -150,7 +150,9 @@ cudaError_t launch_one_step(const ce_sim* s, int in, bool half_kick) {
   if (s->kernel == CE_KERNEL_ROWS && !half_kick) return ce::rows_launch(s->rows, in, s->stream);
   const ce::StepArgs<T> a = make_step_args<T>(s, in, half_kick);
   if (s->kernel == CE_KERNEL_SWEEP) return ce::launch_step_sweep<T>(a, s->plan, s->stream);
-  if (s->kernel == CE_KERNEL_PLANES) return ce::launch_step_planes<T>(a, s->planes, s->stream);
+  if (s->kernel == CE_KERNEL_PLANES)
+    return s->dims == 3 ? ce::launch_step_planes<T>(a, s->planes, s->stream)
+                        : ce::launch_step_lines<T>(a, s->lines, s->stream);
   return ce::launch_step_generic<T>(a, s->generic_blocks, s->stream);
 }
 
@@ -354,8 +356,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const bool rows_ok = cfg->N % (cfg->precision == CE_F32 ? 4 : 2) == 0;
   if (cfg->kernel == CE_KERNEL_ROWS && !rows_ok)
     return fail(CE_EINVAL, "ce_create: the row kernel needs N a multiple of 4 (FP32) or 2 (FP64)");
-  if (cfg->kernel == CE_KERNEL_PLANES && cfg->dims != 3)
-    return fail(CE_EINVAL, "ce_create: the plane-sweep kernel needs dims == 3");
+  if (cfg->kernel == CE_KERNEL_PLANES && cfg->dims < 2)
+    return fail(CE_EINVAL, "ce_create: the plane/line-sweep kernel needs dims 2 or 3");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {
@@ -375,9 +377,9 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
   // Automatic choice.  FP32: the z-sweep kernel where it applies, else the row
-  // kernel for 2D and 3D lattices it takes, else in 3D the plane-sweep kernel
-  // (odd and small sides), else the generic kernel (1D lattices, 2D sides the
-  // row kernel does not take).  FP64 is bound by the FP64 rate, and there
+  // kernel for 2D and 3D lattices it takes, else the plane-sweep kernel (3D) or
+  // the line-sweep kernel (2D) for odd and small sides, else (1D lattices) the
+  // generic kernel.  FP64 is bound by the FP64 rate, and there
   // the generic kernel's two-pass form (each site's g formed once) measured
   // faster than both the z-sweep kernel (256^3: 1090 against 1141 us, tuned
   // plan) and the row kernel (288^3: 1540 against 2967 us): the generic kernel,
@@ -385,7 +387,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const bool sweep_hinted = cfg->tile_rows != 0 || cfg->stages != 0 || cfg->zchunks != 0;
   const bool rows_auto = rows_ok && cfg->precision == CE_F32 && cfg->dims >= 2 &&
                          cfg->N >= (cfg->dims == 3 ? kRowsMinN3 : kRowsMinN2);
-  const bool planes_auto = cfg->precision == CE_F32 && cfg->dims == 3;
+  // (2D below side 512 the generic kernel starts faster: 257^2 12.7 against 16.9 us)
+  const bool planes_auto = cfg->precision == CE_F32 && (cfg->dims == 3 || (cfg->dims == 2 && cfg->N >= kRowsMinN2));
   if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
   else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
   else if (cfg->kernel == CE_KERNEL_PLANES) s->kernel = CE_KERNEL_PLANES;
@@ -434,9 +437,12 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
     sweep_blocks = std::max<int64_t>((int64_t)s->plan.gx * s->plan.gy * s->plan.gz, (s->N / tx) * (s->N / 4) * (s->N / 2));
   }
   int64_t planes_blocks = 0;
-  if (s->kernel == CE_KERNEL_PLANES) {
+  if (s->kernel == CE_KERNEL_PLANES && s->dims == 3) {
     s->planes = ce::planes_plan(s->N, s->nf, s->prec, s->sms);
     planes_blocks = (int64_t)s->planes.gx * s->planes.gy * s->planes.gz;
+  } else if (s->kernel == CE_KERNEL_PLANES) {
+    s->lines = ce::lines_plan(s->N, s->nf, s->prec, s->sms);
+    planes_blocks = (int64_t)s->lines.gx * s->lines.gy;
   }
   int64_t nblk = std::max<int64_t>(std::max<int64_t>(s->generic_blocks, std::max(sweep_blocks, planes_blocks)), 1);
   int64_t plen = std::max<int64_t>(2 * nblk, (int64_t)s->diag_blocks_max * 17);

@@ -156,6 +156,14 @@ struct PlanesPlan {
   int gx, gy, gz, zlen, sx;
 };
 PlanesPlan planes_plan(int64_t N, int nf, int prec, int sms);
+// 2D line-sweep kernel with plain loads (any N): blocks of 8 strips of 32
+// sites in x, y-chunks of ylen rows.
+struct LinesPlan {
+  int gx, gy, ylen;
+};
+LinesPlan lines_plan(int64_t N, int nf, int prec, int sms);
+template <typename T> cudaError_t launch_step_lines(const StepArgs<T>& a, const LinesPlan& plan,
+                                                    cudaStream_t st);
 template <typename T> cudaError_t launch_step_planes(const StepArgs<T>& a, const PlanesPlan& plan,
                                                      cudaStream_t st);
 namespace sweep {
@@ -199,6 +207,7 @@ struct ce_sim {
   int diag_blocks_max = 8;     // grid cap of the diagnostics pass: 8 blocks per SM
   ce::SweepPlan plan{};
   ce::PlanesPlan planes{};
+  ce::LinesPlan lines{};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
   bool graphs_ok = true;
   int64_t bytes = 0;

@@ -62,6 +62,7 @@ BAD = [
     (dict(dims=3, N=1 << 12), "2^34"),
     (dict(dims=2, N=100, kernel="sweep"), "z-sweep"),
     (dict(N=18, precision="f32", kernel="rows"), "row kernel"),
+    (dict(dims=1, N=64, dt=0.004, kernel="planes"), "line-sweep"),
     (dict(tile_rows=12), "tile_rows"),
     (dict(tile_rows=2), "tile_rows"),
     (dict(stages=9), "stages"),

@@ -406,7 +406,9 @@ def auto_kernel(capi, dims, N, precision):
     """The kernel ce_create picks by itself (no plan hints).  FP32: the z-sweep
     kernel for 3D sides that are multiples of its tile, the row kernel for other
     2D/3D lattices it takes with sides >= 96 (3D) or 512 (2D), the plane-sweep
-    kernel for the other 3D lattices, the generic kernel for the rest.  FP64:
+    kernel (CE_KERNEL_PLANES) for the other 3D lattices and the line-sweep kernel
+    (the same id) for the other 2D sides >= 512, the generic kernel for the rest.
+    FP64:
     the generic kernel (its two-pass form in 2D/3D)."""
     if precision == "f64":
         return capi.CE_KERNEL_GENERIC
@@ -414,7 +416,7 @@ def auto_kernel(capi, dims, N, precision):
         return capi.CE_KERNEL_SWEEP
     if dims >= 2 and N % 4 == 0 and N >= (96 if dims == 3 else 512):
         return capi.CE_KERNEL_ROWS
-    if dims == 3:
+    if dims == 3 or (dims == 2 and N >= 512):
         return capi.CE_KERNEL_PLANES
     return capi.CE_KERNEL_GENERIC
 
@@ -481,3 +483,56 @@ def test_planes_kernel_fields_equal_generic_fp32(gpu_capi, N):
         (fa, va, sa), (fb, vb, sb) = out
         assert np.array_equal(fa, fb) and np.array_equal(va, vb), (N, expansion)
         assert abs(sa.a - sb.a) <= 1e-15 * sb.a
+
+
+# 2D line-sweep kernel: N, nf, q: every neighbour wraps (3), a 1-site-wide last
+# strip (33, 65: the right halo is formed by lane 1 of that strip), ragged (37,
+# 101), a side that is a multiple of 32 (the right halo on lane 31)
+LINES_CASES = [(3, 2, (1.2,)), (33, 2, (1.2,)), (37, 3, (0.8, 5.0)), (65, 1, ()), (96, 4, (0.8, 5.0, 40.0)),
+               (101, 2, (1.2,))]
+
+
+@pytest.mark.parametrize("N,nf,q", LINES_CASES, ids=[f"N{c[0]}_nf{c[1]}" for c in LINES_CASES])
+def test_lines_kernel_fp64_vs_oracle(gpu_capi, orc, N, nf, q):
+    """The 2D line-sweep kernel (CE_KERNEL_PLANES in 2D) against the oracle over
+    100 steps with expansion, FP64."""
+    L = 20.0 if N > 5 else 3.0
+    ref, sim, f, v, sc = run_pair(orc, gpu_capi, 2, N, L, 0.02, nf, q, True, 100, kernel="planes", amp=1e-2)
+    with sim:
+        assert sim.kernel == gpu_capi.CE_KERNEL_PLANES
+        assert per_field_err(f, ref.f, nf) <= TOL64
+        assert per_field_err(v, ref.v, nf) <= TOL64
+        assert abs(sc.a - ref.scale.a) / ref.scale.a <= TOL64
+        assert abs(sc.ap_half - ref.scale.ap) / abs(ref.scale.ap) <= TOL64
+
+
+@pytest.mark.parametrize("N", [3, 33, 37, 101, 1001])
+def test_lines_kernel_fields_equal_generic_fp32(gpu_capi, N):
+    """Per site the 2D line-sweep kernel does the generic kernel's arithmetic:
+    FP32 fields bit-identical over many steps without expansion and after one
+    step with it."""
+    nf, q = 2, (1.2,)
+    f0, u0 = lattice_ics(2, N, 20.0, nf, q=q, seed=4, amp=1e-2)
+    dt = courant_dt(2, N, 20.0, 1.0, q)
+    for expansion, steps in ((False, 20), (True, 1)):
+        out = []
+        for kernel in ("planes", "generic"):
+            with gpu_capi.Simulation(dims=2, N=N, L=20.0, dt=dt, nfields=nf, q=q, expansion=expansion,
+                                     precision="f32", kernel=kernel) as sim:
+                assert sim.kernel == (gpu_capi.CE_KERNEL_PLANES if kernel == "planes" else gpu_capi.CE_KERNEL_GENERIC)
+                sim.set_fields(f0, u0)
+                sim.step(steps)
+                out.append(sim.get_fields(gpu_capi.CE_VEL_STAGGERED))
+        (fa, va, sa), (fb, vb, sb) = out
+        assert np.array_equal(fa, fb) and np.array_equal(va, vb), (N, expansion)
+        assert abs(sa.a - sb.a) <= 1e-15 * sb.a
+
+
+@pytest.mark.parametrize("N,expected", [(1001, "planes"), (6001, "planes"), (257, "generic"), (1024, "rows")])
+def test_automatic_choice_2d_fp32(gpu_capi, N, expected):
+    """FP32 2D: the row kernel for sides >= 512 that are multiples of 4, the
+    line-sweep kernel for the other sides >= 512, the generic kernel below."""
+    ids = {"planes": gpu_capi.CE_KERNEL_PLANES, "generic": gpu_capi.CE_KERNEL_GENERIC, "rows": gpu_capi.CE_KERNEL_ROWS}
+    with gpu_capi.Simulation(dims=2, N=N, L=20.0, dt=courant_dt(2, N, 20.0, 1.0, (1.2,)), nfields=2, q=(1.2,),
+                             precision="f32") as sim:
+        assert sim.kernel == ids[expected] == auto_kernel(gpu_capi, 2, N, "f32")
