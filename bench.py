@@ -288,7 +288,8 @@ def roofline_of(w, precision, ms_per_step, hbm_peak, peak_kind, kernel):
     esize = 4 if precision == "f32" else 8
     alg = 4 * esize * w["nf"] * S          # read f, w; write f, w per field and site
     achieved = alg / (ms_per_step / 1e3) / 1e9
-    kname = {"sweep": "k_step_sweep", "rows": "k_step_batched"}.get(kernel, "k_step_generic")
+    kname = {"sweep": "k_step_sweep", "rows": "k_step_batched",
+             "planes": "k_step_cols" if w["dims"] == 3 else "k_step_lines"}.get(kernel, "k_step_generic")
     traffic, note = ncu_traffic(kname, precision, S) if kname in STEP_SOURCES else (None, None)
     out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
            "traffic": traffic, "kernel": kname, "algorithmic_bytes_per_launch": alg, "peak_kind": peak_kind}
@@ -538,7 +539,7 @@ def shapes_mode(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> i
       one k_step_batched launch per step, at two item lengths;
     * batch_3d: homogeneous batches of about 100 M sites of one 3D side;
     * single: one lattice stepped by ce_step with the generic kernel, the row
-      kernel (CE_KERNEL_ROWS, sides that are multiples of 4) and the plane /
+      kernel (CE_KERNEL_ROWS, sides that are multiples of 4) and the column /
       line-sweep kernel (CE_KERNEL_PLANES, 3D / 2D), FP32 and FP64.
 
     CUDA events on the library's stream around `steps` steps after `warmup`;

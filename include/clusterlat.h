@@ -70,17 +70,19 @@ extern "C" {
 
 /* ---- kernel selection (ce_config.kernel) ------------------------------ */
 #define CE_KERNEL_AUTO    0 /* FP32: z-sweep kernel where it applies; else the
-                               row kernel for 2D sides >= 512 and 3D sides >= 96
-                               it takes; else the plane-sweep kernel (3D) or the
-                               line-sweep kernel (2D sides >= 512); else generic.  FP64: generic (its two-pass
+                               row kernel for 2D sides >= 512 and 3D sides >= 256
+                               it takes; else the column kernel (3D) or the
+                               line-sweep kernel (2D sides >= 320); else generic.  FP64: generic (its two-pass
                                form), or the z-sweep kernel when plan hints
                                (tile_rows, stages, zchunks) are given          */
 #define CE_KERNEL_GENERIC 1 /* one thread per site, any d and N              */
 #define CE_KERNEL_SWEEP   2 /* 3D z-sweep kernel (CE_EINVAL if it does not apply) */
 #define CE_KERNEL_ROWS    3 /* the batched row-sweep kernel on this one lattice:
                                any d, N a multiple of 4 (FP32) / 2 (FP64)      */
-#define CE_KERNEL_PLANES  4 /* sweep kernel with plain loads, any N: z-planes in
-                               3D, rows in 2D (CE_EINVAL in 1D)                */
+#define CE_KERNEL_PLANES  4 /* sweep kernel with plain loads and register
+                               neighbours, any N: z-sweeps of warp columns in
+                               3D, y-sweeps of warp strips in 2D (CE_EINVAL
+                               in 1D)                                          */
 
 /* ---- config flags ---------------------------------------------------- */
 #define CE_FLAG_ALLOW_UNSTABLE_DT 1  /* skip the dt < 2/omega_max check       */

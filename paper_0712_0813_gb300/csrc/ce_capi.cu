@@ -31,12 +31,17 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr double kDefaultPhi0OverMpl = 0.342;
 constexpr int64_t kMaxSites = int64_t(1) << 34;
 constexpr int64_t kStagingChunk = int64_t(1) << 22;   // sites per staging chunk
-// Smallest sides for which the automatic choice takes the row kernel (FP32),
-// from timings on single lattices: below them a lattice is a few microseconds
-// of traffic and the plane-sweep kernel (3D; 64^3: 13.1 against 15.8 us, 96^3:
-// 19.2 against 19.0) or the generic kernel (2D) starts faster.
-constexpr int kRowsMinN3 = 96;
+// Smallest sides for which the automatic FP32 choice takes the row kernel
+// (sides that are multiples of 4) and, in 2D, the line-sweep kernel, from
+// timings of single lattices (us per step).  3D below side 256 the column
+// kernel is as fast or faster than the row kernel (96^3: 16.4 against 19.8,
+// 224^3: 77.0 against 81.8, 192^3: 52.7 against 51.5; 288^3: 158.9 against
+// 148.9).  2D below side 512 the row kernel and the line-sweep kernel tie
+// (512^2: 14.6 both), and below 320 the generic kernel starts faster than the
+// line-sweep kernel (257^2: 12.7 against 13.2; 385^2: 15.5 against 12.9).
+constexpr int kRowsMinN3 = 256;
 constexpr int kRowsMinN2 = 512;
+constexpr int kLinesMinN2 = 320;
 constexpr int kGraphSteps = 32;   // steps per captured CUDA graph (even: keeps the ping-pong parity)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device-side wait
 
@@ -151,7 +156,7 @@ cudaError_t launch_one_step(const ce_sim* s, int in, bool half_kick) {
   const ce::StepArgs<T> a = make_step_args<T>(s, in, half_kick);
   if (s->kernel == CE_KERNEL_SWEEP) return ce::launch_step_sweep<T>(a, s->plan, s->stream);
   if (s->kernel == CE_KERNEL_PLANES)
-    return s->dims == 3 ? ce::launch_step_planes<T>(a, s->planes, s->stream)
+    return s->dims == 3 ? ce::launch_step_cols<T>(a, s->cols, s->stream)
                         : ce::launch_step_lines<T>(a, s->lines, s->stream);
   return ce::launch_step_generic<T>(a, s->generic_blocks, s->stream);
 }
@@ -377,9 +382,9 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const double p0m = cfg->phi0_over_mpl > 0.0 ? cfg->phi0_over_mpl : kDefaultPhi0OverMpl;
   s->kappa2 = 8.0 * M_PI / 3.0 * p0m * p0m;
   // Automatic choice.  FP32: the z-sweep kernel where it applies, else the row
-  // kernel for 2D and 3D lattices it takes, else the plane-sweep kernel (3D) or
-  // the line-sweep kernel (2D) for odd and small sides, else (1D lattices) the
-  // generic kernel.  FP64 is bound by the FP64 rate, and there
+  // kernel for the 2D and 3D lattices it takes from the sides above, else the
+  // column kernel (3D) or the line-sweep kernel (2D) for odd and small sides,
+  // else (1D lattices, small 2D sides) the generic kernel.  FP64 is bound by the FP64 rate, and there
   // the generic kernel's two-pass form (each site's g formed once) measured
   // faster than both the z-sweep kernel (256^3: 1090 against 1141 us, tuned
   // plan) and the row kernel (288^3: 1540 against 2967 us): the generic kernel,
@@ -387,8 +392,7 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   const bool sweep_hinted = cfg->tile_rows != 0 || cfg->stages != 0 || cfg->zchunks != 0;
   const bool rows_auto = rows_ok && cfg->precision == CE_F32 && cfg->dims >= 2 &&
                          cfg->N >= (cfg->dims == 3 ? kRowsMinN3 : kRowsMinN2);
-  // (2D below side 512 the generic kernel starts faster: 257^2 12.7 against 16.9 us)
-  const bool planes_auto = cfg->precision == CE_F32 && (cfg->dims == 3 || (cfg->dims == 2 && cfg->N >= kRowsMinN2));
+  const bool planes_auto = cfg->precision == CE_F32 && (cfg->dims == 3 || (cfg->dims == 2 && cfg->N >= kLinesMinN2));
   if (cfg->kernel == CE_KERNEL_GENERIC) s->kernel = CE_KERNEL_GENERIC;
   else if (cfg->kernel == CE_KERNEL_ROWS) s->kernel = CE_KERNEL_ROWS;
   else if (cfg->kernel == CE_KERNEL_PLANES) s->kernel = CE_KERNEL_PLANES;
@@ -438,8 +442,8 @@ int ce_create(const ce_config* cfg, ce_sim** out) {
   }
   int64_t planes_blocks = 0;
   if (s->kernel == CE_KERNEL_PLANES && s->dims == 3) {
-    s->planes = ce::planes_plan(s->N, s->nf, s->prec, s->sms);
-    planes_blocks = (int64_t)s->planes.gx * s->planes.gy * s->planes.gz;
+    s->cols = ce::cols_plan(s->N, s->nf, s->prec, s->sms);
+    planes_blocks = (int64_t)s->cols.gx * s->cols.gz;
   } else if (s->kernel == CE_KERNEL_PLANES) {
     s->lines = ce::lines_plan(s->N, s->nf, s->prec, s->sms);
     planes_blocks = (int64_t)s->lines.gx * s->lines.gy;

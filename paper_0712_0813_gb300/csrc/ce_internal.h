@@ -150,22 +150,21 @@ cudaError_t sweep_prepare(SweepPlan& plan, void* const f[2][4], void* const w[2]
                           int prec, int device, int rows_hint, int stages_hint, int zchunks_hint);
 template <typename T> cudaError_t launch_step_sweep(const StepArgs<T>& a, const SweepPlan& plan,
                                                     cudaStream_t st);
-// 3D plane-sweep kernel with plain loads (any N): grid of (32 sx) x 8 site
-// columns (sx sites per lane, 1 or 2) and z-chunks of zlen planes.
-struct PlanesPlan {
-  int gx, gy, gz, zlen, sx;
+// 3D column kernel with plain loads (any N): warps over strips of 30 x-sites
+// by a group of ty rows, 4 warps per block, z-chunks of zlen planes.
+struct ColsPlan {
+  int nstrips, ngroups, gx, gz, zlen, ty;
 };
-PlanesPlan planes_plan(int64_t N, int nf, int prec, int sms);
-// 2D line-sweep kernel with plain loads (any N): blocks of 8 strips of 32
+ColsPlan cols_plan(int64_t N, int nf, int prec, int sms);
+template <typename T> cudaError_t launch_step_cols(const StepArgs<T>& a, const ColsPlan& plan, cudaStream_t st);
+// 2D line-sweep kernel with plain loads (any N): blocks of 8 strips of 30
 // sites in x, y-chunks of ylen rows.
 struct LinesPlan {
-  int gx, gy, ylen;
+  int nstrips, gx, gy, ylen;
 };
 LinesPlan lines_plan(int64_t N, int nf, int prec, int sms);
 template <typename T> cudaError_t launch_step_lines(const StepArgs<T>& a, const LinesPlan& plan,
                                                     cudaStream_t st);
-template <typename T> cudaError_t launch_step_planes(const StepArgs<T>& a, const PlanesPlan& plan,
-                                                     cudaStream_t st);
 namespace sweep {
 cudaError_t launch_f32(int variant, const StepArgs<float>& a, const SweepMaps& m, dim3 grid, size_t smem,
                        cudaStream_t st);
@@ -206,7 +205,7 @@ struct ce_sim {
   int generic_blocks = 1;
   int diag_blocks_max = 8;     // grid cap of the diagnostics pass: 8 blocks per SM
   ce::SweepPlan plan{};
-  ce::PlanesPlan planes{};
+  ce::ColsPlan cols{};
   ce::LinesPlan lines{};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer set 0 / 1
   bool graphs_ok = true;

@@ -1,8 +1,7 @@
-// ce_lines2d.cu -- the 2D step for any side N: each warp sweeps a 32-site
-// strip of x along a chunk of rows y, with plain coalesced loads (no
-// alignment needed, so odd sides work), y-neighbours carried in registers and
-// x-neighbours exchanged by warp shuffles: no shared memory, no block barrier
-// in the sweep.
+// ce_lines2d.cu -- the 2D step for any side N: each warp sweeps a strip of 30
+// x-sites along a chunk of rows y, with plain coalesced loads (no alignment
+// needed, so odd sides work), y-neighbours carried in registers and
+// x-neighbours exchanged by warp shuffles: no shared memory, no block barrier.
 //
 // Per site the arithmetic is the generic kernel's (arXiv:0712.0813 Sec. III
 // staggered leapfrog, fused: v = w + c f, g = f + dt v, lap g from the 2d
@@ -10,14 +9,16 @@
 // f_out = g), so the fields agree with k_step_generic bit for bit; only the
 // global sums are added in another order.
 //
-// Warp w of block b owns the strip x0 = 32 (8 b.x + w) .. x0 + nx - 1 (nx <= 32)
-// and the rows y0 .. y1 - 1 of chunk b.y; it forms g on the rows y0 - 1 .. y1
-// (mod N).  The strip's x-halo: lane 0 also forms g at x0 - 1; the site
-// x0 + nx (mod N) is formed by lane nx as if it were its own when nx < 32 (the
-// shuffle then brings it to lane nx - 1), and by lane 31 beside its own
-// otherwise.  Each thread keeps the loads of the next two rows in
-// flight (registers), so a warp has 2 x 4 NF values of 4 or 8 bytes per lane
-// outstanding.
+// Warp w of block b owns the strip x0 = 30 (8 b.x + w) .. x0 + nx - 1 (nx <= 30)
+// and the rows y0 .. y1 - 1 of chunk b.y, and forms g on the rows y0 - 1 .. y1
+// (mod N).  Lane l holds the column x0 - 1 + l (mod N): lanes 1 .. nx update
+// their sites, lanes 0 and nx + 1 hold the strip's x-halo (lanes past nx + 1
+// repeat lane nx + 1's column), so one load instruction per field and array
+// brings a row with its halo and the shuffles give every updated site both
+// x-neighbours.  Each lane keeps the loads of the next DL rows in flight in a
+// ring of registers (DL = 8 / 6 / 4 for 1 / 2 / 3-4 fields): 2-3 KB per warp,
+// which the latency of HBM needs.  Neighbouring chunks sweep in opposite directions, so
+// the two chunks that share a boundary row read it at about the same time.
 #include <cstdint>
 
 #include "ce_device.cuh"
@@ -28,128 +29,112 @@ namespace {
 
 constexpr int kLineWarps = 8;
 constexpr int kLineThreads = 32 * kLineWarps;
+constexpr int kStrip = 30;   // sites a warp updates along x
 
-template <typename T, int NF>
-__global__ void __launch_bounds__(kLineThreads) k_step_lines(const StepArgs<T> p, int ylen) {
+// rows of loads in flight per lane (6001^2, 2 fields: 4 rows 229.0 us, 6 rows
+// 223.8, 8 rows 228.9, the last at 3 instead of 4 blocks per SM; 16001^2: 1642,
+// 1497, 1541 us)
+template <int NF>
+struct LineDepth {
+  static constexpr int value = NF == 1 ? 8 : (NF == 2 ? 6 : 4);
+};
+
+template <typename T, int NF, int DL>
+__global__ void __launch_bounds__(kLineThreads) k_step_lines(const StepArgs<T> p, int nstrips, int ylen) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t N = p.N;
-  const int64_t x0 = ((int64_t)blockIdx.x * kLineWarps + warp) * 32;
-  const int y0 = blockIdx.y * ylen;
-  const int y1 = (int)min((int64_t)y0 + ylen, N);
+  const int64_t wg = (int64_t)blockIdx.x * kLineWarps + warp;
   T g2acc = T(0), vacc = T(0), g2loc = T(0), vloc = T(0);   // two-level sums (see k_step_generic)
-  if (x0 < N) {
-    const int nx = (int)min((int64_t)32, N - x0);
-    const int64_t xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + nx == N ? 0 : x0 + nx;
-    const bool site = lane < nx;                              // updates a site
-    const bool act = lane <= nx && lane < 32;                 // forms a g: the site, or lane nx the right halo
-    const bool hl = lane == 0, hr = nx == 32 && lane == 31;   // halo g beside the own one
-    const int64_t xs = lane < nx ? x0 + lane : xr;
+  if (wg < nstrips) {
+    const int64_t x0 = wg * kStrip;
+    const int nx = (int)min((int64_t)kStrip, N - x0);
+    int64_t xs = x0 - 1 + min(lane, nx + 1);
+    xs = xs < 0 ? xs + N : (xs >= N ? xs - N : xs);
+    const bool site = lane >= 1 && lane <= nx;
+    const int y0 = blockIdx.y * ylen;
+    const int y1 = (int)min((int64_t)y0 + ylen, N);
+    const int n = y1 - y0 + 2;                                 // rows y0 - 1 .. y1
+    const bool down = (blockIdx.y & 1u) != 0;
+    // row k of the sweep: y0 - 1 + k upwards, y1 - k downwards (mod N)
+    const auto row_off = [&](int k) -> int64_t {
+      int64_t y = down ? (int64_t)y1 - k : (int64_t)y0 - 1 + k;
+      y = y < 0 ? y + N : (y >= N ? y - N : y);
+      return y * N + xs;
+    };
     const T c = (T)p.sc_in->c;
     const T dd = p.dt_drift, kk = p.dt_kick, idx2 = p.inv_dx2;
     const T q[3] = {p.q[0], p.q[1], p.q[2]};
-    const int n = y1 - y0 + 2;                                // staged rows y0 - 1 .. y1
-    int64_t yrow = y0 == 0 ? N - 1 : y0 - 1;                  // row of the next load
-    // loads in flight: A = the next row, B = the one after it
-    T fa[NF], wa[NF], fha[NF], wha[NF], fb[NF], wb[NF], fhb[NF], whb[NF];
-    const auto fetch = [&](T (&f)[NF], T (&w)[NF], T (&fh)[NF], T (&wh)[NF]) {
-      const int64_t base = yrow * N;
+    T lf[DL][NF], lw[DL][NF];
+    const auto issue = [&](int k, int slot) {
+      const int64_t o = row_off(k);
 #pragma unroll
       for (int i = 0; i < NF; ++i) {
-        if (act) {
-          f[i] = __ldg(p.f_in[i] + base + xs);
-          w[i] = __ldg(p.w_in[i] + base + xs);
-        }
-        if (hl || hr) {
-          const int64_t hx = hl ? xl : xr;
-          fh[i] = __ldg(p.f_in[i] + base + hx);
-          wh[i] = __ldg(p.w_in[i] + base + hx);
-        }
+        lf[slot][i] = __ldg(p.f_in[i] + o);
+        lw[slot][i] = __ldg(p.w_in[i] + o);
       }
-      yrow = yrow == N - 1 ? 0 : yrow + 1;
     };
-    T gm[NF], gc[NF], gp[NF], vc[NF], vn[NF], hc[NF], hp[NF];
 #pragma unroll
-    for (int i = 0; i < NF; ++i) gm[i] = gc[i] = gp[i] = vc[i] = vn[i] = hc[i] = hp[i] = T(0);
+    for (int s = 0; s < DL; ++s)
+      if (s < n) issue(s, s);
+    T gm[NF], gc[NF], gp[NF], vc[NF], vp[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) gm[i] = gc[i] = gp[i] = vc[i] = vp[i] = T(0);
     int since_flush = 0;
-    int64_t upd = (int64_t)y0 * N + xs;                       // output offset of the next updated row
-    // staged row j (loads in f, w, fh, wh): form its g into gp (own site) and
-    // hp (halo site); then (j >= 2) update row j - 1
-    const auto stage = [&](int j, const T (&f)[NF], const T (&w)[NF], const T (&fh)[NF], const T (&wh)[NF]) {
+    for (int k0 = 0; k0 < n; k0 += DL) {
 #pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        gm[i] = gc[i];
-        gc[i] = gp[i];
-        vc[i] = vn[i];
-        hc[i] = hp[i];
-        if (act) {
-          vn[i] = fmaT(c, f[i], w[i]);
-          gp[i] = fmaT(dd, vn[i], f[i]);
-        }
-        if (hl || hr) hp[i] = fmaT(dd, fmaT(c, fh[i], wh[i]), fh[i]);
-      }
-      if (j < 2) return;
-      T xms[NF], xps[NF];
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {   // every lane takes part in the shuffles
-        xms[i] = __shfl_up_sync(0xffffffffu, gc[i], 1);
-        xps[i] = __shfl_down_sync(0xffffffffu, gc[i], 1);
-      }
-      if (!site) return;
-      T lap[NF];
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        const T g = gc[i];
-        const T xm = hl ? hc[i] : xms[i];
-        const T xp = hr ? hc[i] : xps[i];
-        T acc = T(0);
-        acc += (xp + xm) - T(2) * g;
-        T df = xp - g;
-        g2loc = fmaT(df, df, g2loc);
-        acc += (gp[i] + gm[i]) - T(2) * g;
-        df = gp[i] - g;
-        g2loc = fmaT(df, df, g2loc);
-        lap[i] = acc * idx2;
-      }
-      T dv[NF], vs;
-      model_dv<T, NF>(gc, q, dv, vs);
-      vloc += vs;
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        __stcs(p.w_out[i] + upd, fmaT(kk, lap[i] - dv[i], vc[i]));
-        __stcs(p.f_out[i] + upd, gc[i]);
-      }
-      upd += N;   // the chunk's rows y0 .. y1 - 1 do not wrap
-      if (++since_flush == 16) {
-        g2acc += g2loc;
-        vacc += vloc;
-        g2loc = T(0);
-        vloc = T(0);
-        since_flush = 0;
-      }
-    };
-    fetch(fa, wa, fha, wha);
-    if (n > 1) fetch(fb, wb, fhb, whb);
-    for (int j = 0; j < n; j += 2) {
-      T f[NF], w[NF], fh[NF], wh[NF];
-#pragma unroll
-      for (int i = 0; i < NF; ++i) {
-        f[i] = fa[i];
-        w[i] = wa[i];
-        fh[i] = fha[i];
-        wh[i] = wha[i];
-      }
-      if (j + 2 < n) fetch(fa, wa, fha, wha);
-      stage(j, f, w, fh, wh);
-      if (j + 1 < n) {
+      for (int s = 0; s < DL; ++s) {
+        const int j = k0 + s;
+        if (j >= n) break;
 #pragma unroll
         for (int i = 0; i < NF; ++i) {
-          f[i] = fb[i];
-          w[i] = wb[i];
-          fh[i] = fhb[i];
-          wh[i] = whb[i];
+          const T v = fmaT(c, lf[s][i], lw[s][i]);
+          gm[i] = gc[i];
+          gc[i] = gp[i];
+          gp[i] = fmaT(dd, v, lf[s][i]);
+          vc[i] = vp[i];
+          vp[i] = v;
         }
-        if (j + 3 < n) fetch(fb, wb, fhb, whb);
-        stage(j + 1, f, w, fh, wh);
+        if (j + DL < n) issue(j + DL, s);
+        if (j < 2) continue;
+        // update row j - 1 of the sweep; y + 1 is the next row upwards, the previous one downwards
+        T xms[NF], xps[NF];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {   // every lane takes part in the shuffles
+          xms[i] = __shfl_up_sync(0xffffffffu, gc[i], 1);
+          xps[i] = __shfl_down_sync(0xffffffffu, gc[i], 1);
+        }
+        if (site) {
+          T lap[NF];
+#pragma unroll
+          for (int i = 0; i < NF; ++i) {
+            const T g = gc[i];
+            const T yp = down ? gm[i] : gp[i], ym = down ? gp[i] : gm[i];
+            T acc = T(0);
+            acc += (xps[i] + xms[i]) - T(2) * g;
+            T df = xps[i] - g;
+            g2loc = fmaT(df, df, g2loc);
+            acc += (yp + ym) - T(2) * g;
+            df = yp - g;
+            g2loc = fmaT(df, df, g2loc);
+            lap[i] = acc * idx2;
+          }
+          T dv[NF], vs;
+          model_dv<T, NF>(gc, q, dv, vs);
+          vloc += vs;
+          const int64_t o = row_off(j - 1);
+#pragma unroll
+          for (int i = 0; i < NF; ++i) {
+            __stcs(p.w_out[i] + o, fmaT(kk, lap[i] - dv[i], vc[i]));
+            __stcs(p.f_out[i] + o, gc[i]);
+          }
+        }
+        if (++since_flush == 16) {
+          g2acc += g2loc;
+          vacc += vloc;
+          g2loc = T(0);
+          vloc = T(0);
+          since_flush = 0;
+        }
       }
     }
   }
@@ -158,14 +143,15 @@ __global__ void __launch_bounds__(kLineThreads) k_step_lines(const StepArgs<T> p
 
 template <typename T, int NF>
 cudaError_t launch_nf(const StepArgs<T>& a, const LinesPlan& pl, cudaStream_t st) {
-  k_step_lines<T, NF><<<dim3(pl.gx, pl.gy), kLineThreads, 0, st>>>(a, pl.ylen);
+  k_step_lines<T, NF, LineDepth<NF>::value><<<dim3(pl.gx, pl.gy), kLineThreads, 0, st>>>(a, pl.nstrips, pl.ylen);
   return cudaGetLastError();
 }
 
 template <typename T, int NF>
 int blocks_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_lines<T, NF>, kLineThreads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_lines<T, NF, LineDepth<NF>::value>, kLineThreads,
+                                                    0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -174,13 +160,15 @@ int blocks_per_sm() {
 
 }  // namespace
 
-// Grid of the line-sweep kernel: 8 strips of 32 sites per block in x, y split
-// into chunks so that about two waves of resident blocks are busy, with chunks
-// of at least 16 rows (each chunk forms 2 halo rows besides its own).
+// Grid of the line-sweep kernel: 8 strips of 30 sites per block in x, and the
+// count of y-chunks with the least predicted time: every block sweeps one
+// chunk (its rows, 2 halo rows and a start-up of about 3), the blocks run in
+// waves of the resident blocks, a partial wave costing a whole one.  Chunks of
+// at least 8 rows.
 LinesPlan lines_plan(int64_t N, int nf, int prec, int sms) {
   LinesPlan pl{};
-  const int64_t strips = (N + 31) / 32;
-  pl.gx = (int)((strips + kLineWarps - 1) / kLineWarps);
+  pl.nstrips = (int)((N + kStrip - 1) / kStrip);
+  pl.gx = (int)((pl.nstrips + kLineWarps - 1) / kLineWarps);
   int per_sm;
   if (prec == CE_F32)
     per_sm = nf == 1 ? blocks_per_sm<float, 1>() : nf == 2 ? blocks_per_sm<float, 2>()
@@ -188,9 +176,18 @@ LinesPlan lines_plan(int64_t N, int nf, int prec, int sms) {
   else
     per_sm = nf == 1 ? blocks_per_sm<double, 1>() : nf == 2 ? blocks_per_sm<double, 2>()
            : nf == 3 ? blocks_per_sm<double, 3>() : blocks_per_sm<double, 4>();
-  const int64_t want = std::max<int64_t>(1, (2LL * per_sm * sms + pl.gx - 1) / pl.gx);
-  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(want, N / 16));
-  pl.ylen = (int)((N + gy - 1) / gy);
+  const int64_t slots = (int64_t)per_sm * sms;
+  double best = 1e300;
+  pl.ylen = (int)N;
+  for (int64_t gy = 1; gy <= std::max<int64_t>(1, N / 8); ++gy) {
+    const int64_t ylen = (N + gy - 1) / gy, g = (N + ylen - 1) / ylen;
+    const int64_t waves = (pl.gx * g + slots - 1) / slots;
+    const double t = (double)waves * (double)(ylen + 5);
+    if (t < best * (1.0 - 1e-9)) {
+      best = t;
+      pl.ylen = (int)ylen;
+    }
+  }
   pl.gy = (int)((N + pl.ylen - 1) / pl.ylen);
   return pl;
 }
