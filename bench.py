@@ -585,7 +585,8 @@ def shapes_mode(steps: int = 100, warmup: int = 20, item_lengths=(64, 128)) -> i
         print(json.dumps(row), flush=True)
         for sim in sims:
             sim.close()
-    for dims, N in ((1, 65536), (2, 1023), (2, 1024), (2, 6000), (2, 6001), (3, 48), (3, 64), (3, 95), (3, 96),
+    for dims, N in ((1, 65536), (2, 257), (2, 385), (2, 1023), (2, 1024), (2, 6000), (2, 6001), (3, 48), (3, 64),
+                    (3, 95), (3, 96),
                     (3, 160), (3, 192), (3, 255), (3, 288), (3, 383), (3, 448), (3, 511)):
         big = N ** dims >= 1 << 22
         f0, u0 = lattice_ics(dims, N, 20.0, 2, q=(1.2,), seed=3, amp=1e-2, backend="torch" if big else "numpy")
