@@ -298,6 +298,28 @@ def roofline_of(w, precision, ms_per_step, hbm_peak, peak_kind, kernel):
     return out
 
 
+# FP64 instructions per site of the generic kernel's two-pass FP64 step, 3D, 2
+# fields (ncu, 256^3: k_drift_g 2 per field and site, k_kick_from_g 14.1; each
+# DADD, DMUL or DFMA takes one slot of the FP64 pipe), and the pipe's rate:
+# GB300's nominal FP64 1.25 TFLOP/s counts a DFMA as 2 flops, so 0.625 T
+# instructions/s (152 SMs x 2 FP64 lanes x 2.07 GHz = 0.629 T).
+FP64_OPS_PER_SITE_2F_3D = 32.2
+FP64_PIPE_PEAK_TOPS = 0.625
+
+
+def fp64_alu_roofline(w, gsites_per_s: float, kernel: str, hbm_peak: float):
+    """The plain FP64 path is bound by GB300's FP64 pipe, not by HBM: its
+    roofline in FP64 instructions per second (2-field 3D lattices on the generic
+    kernel's two passes, whose per-site count was measured)."""
+    if not (w["dims"] == 3 and w["nf"] == 2 and kernel == "generic"):
+        return None
+    achieved = gsites_per_s * FP64_OPS_PER_SITE_2F_3D / 1e3
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PIPE_PEAK_TOPS, "unit": "T FP64 instructions/s",
+            "frac": achieved / FP64_PIPE_PEAK_TOPS, "ops_per_site": FP64_OPS_PER_SITE_2F_3D,
+            "peak_kind": "nominal FP64 rate (1.25 TFLOP/s, a DFMA = 2 flops = one pipe slot)",
+            "hbm_frac": gsites_per_s * 4 * 8 * w["nf"] / hbm_peak}
+
+
 def cube256_leg(capi, torch, steps: int, warmup: int, hbm_peak: float, peak_kind: str):
     """The expanding 256^3 lattice (the 5000-step configuration), FP32 with the
     autotuned z-sweep plan, timed for `steps` steps on the device."""
@@ -806,7 +828,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": f"state {4 * esize * w['nf'] * S / 1e6:.0f} MB > L2 (129 MB); no flush needed"},
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
-                           "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64},
+                           "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64,
+                           "roofline": fp64_alu_roofline(w, value64, kernel64, hbm_peak)},
             "roofline": roofline,
             "fp32_vs_fp64": fp32_vs_fp64,
             "cube256": cube256,
