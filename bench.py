@@ -683,7 +683,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU seconds per oracle leg")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the serving leg (0: skip)")
     ap.add_argument("--serve-fp64", default="measured", choices=["measured", "model"])
-    ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--batch-steps", type=int, default=3000, help="steps of the batched mix (its full run)")
     ap.add_argument("--seq-steps", type=int, default=64, help="steps per lattice of the one-at-a-time baselines")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batched leg")
     ap.add_argument("--plan", default=None,
