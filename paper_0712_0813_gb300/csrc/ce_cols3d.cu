@@ -28,6 +28,7 @@
 
 #include "ce_device.cuh"
 #include "ce_internal.h"
+#include "ce_plan.h"
 
 namespace ce {
 namespace {
@@ -236,10 +237,8 @@ void rows_and_occupancy_nf(int nf, bool narrow, int& ty, int& per_sm) {
 }  // namespace
 
 // Grid of the column kernel: warps over (strip, row group), 4 per block, and
-// the z-chunk count with the least predicted time: every block of a launch
-// sweeps one chunk (its planes, 2 halo planes and a start-up of about 3), and
-// the blocks run in waves of `per_sm` x `sms` resident blocks, a partial wave
-// costing a whole one.  Chunks of at least 4 planes.
+// the z-chunk length of the wave model (plan::wave_chunk_length: chunks of at
+// least 4 planes, each costing 5 more for its halo planes and start-up).
 ColsPlan cols_plan(int64_t N, int nf, int prec, int sms) {
   ColsPlan pl{};
   int per_sm = 1;
@@ -249,18 +248,7 @@ ColsPlan cols_plan(int64_t N, int nf, int prec, int sms) {
   pl.ngroups = (int)((N + pl.ty - 1) / pl.ty);
   const int64_t warps = (int64_t)pl.nstrips * pl.ngroups;
   pl.gx = (int)((warps + kColWarps - 1) / kColWarps);
-  const int64_t slots = (int64_t)per_sm * sms;
-  double best = 1e300;
-  pl.zlen = (int)N;
-  for (int64_t gz = 1; gz <= std::max<int64_t>(1, N / 4); ++gz) {
-    const int64_t zlen = (N + gz - 1) / gz, g = (N + zlen - 1) / zlen;
-    const int64_t waves = (pl.gx * g + slots - 1) / slots;
-    const double t = (double)waves * (double)(zlen + 5);
-    if (t < best * (1.0 - 1e-9)) {
-      best = t;
-      pl.zlen = (int)zlen;
-    }
-  }
+  pl.zlen = plan::wave_chunk_length(N, pl.gx, (int64_t)per_sm * sms, 4, 5.0);   // ce_plan.h
   pl.gz = (int)((N + pl.zlen - 1) / pl.zlen);
   return pl;
 }

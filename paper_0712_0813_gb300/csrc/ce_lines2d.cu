@@ -23,6 +23,7 @@
 
 #include "ce_device.cuh"
 #include "ce_internal.h"
+#include "ce_plan.h"
 
 namespace ce {
 namespace {
@@ -161,10 +162,8 @@ int blocks_per_sm() {
 }  // namespace
 
 // Grid of the line-sweep kernel: 8 strips of 30 sites per block in x, and the
-// count of y-chunks with the least predicted time: every block sweeps one
-// chunk (its rows, 2 halo rows and a start-up of about 3), the blocks run in
-// waves of the resident blocks, a partial wave costing a whole one.  Chunks of
-// at least 8 rows.
+// row-chunk length of the wave model (plan::wave_chunk_length: chunks of at
+// least 8 rows, each costing 5 more for its halo rows and start-up).
 LinesPlan lines_plan(int64_t N, int nf, int prec, int sms) {
   LinesPlan pl{};
   pl.nstrips = (int)((N + kStrip - 1) / kStrip);
@@ -176,18 +175,7 @@ LinesPlan lines_plan(int64_t N, int nf, int prec, int sms) {
   else
     per_sm = nf == 1 ? blocks_per_sm<double, 1>() : nf == 2 ? blocks_per_sm<double, 2>()
            : nf == 3 ? blocks_per_sm<double, 3>() : blocks_per_sm<double, 4>();
-  const int64_t slots = (int64_t)per_sm * sms;
-  double best = 1e300;
-  pl.ylen = (int)N;
-  for (int64_t gy = 1; gy <= std::max<int64_t>(1, N / 8); ++gy) {
-    const int64_t ylen = (N + gy - 1) / gy, g = (N + ylen - 1) / ylen;
-    const int64_t waves = (pl.gx * g + slots - 1) / slots;
-    const double t = (double)waves * (double)(ylen + 5);
-    if (t < best * (1.0 - 1e-9)) {
-      best = t;
-      pl.ylen = (int)ylen;
-    }
-  }
+  pl.ylen = plan::wave_chunk_length(N, pl.gx, (int64_t)per_sm * sms, 8, 5.0);   // ce_plan.h
   pl.gy = (int)((N + pl.ylen - 1) / pl.ylen);
   return pl;
 }

@@ -170,5 +170,28 @@ inline int auto_zchunks(int64_t N, int64_t cols, int per_sm, int sms) {
   return best_gz;
 }
 
+// Chunk length along the sweep axis for the kernels whose blocks each sweep one
+// chunk of an N-long axis (the column kernel's z-chunks, the line-sweep
+// kernel's row chunks): the length with the least predicted time, where the
+// launch's blocks (`blocks_per_chunk` per chunk) run in waves of `slots`
+// resident blocks and each wave costs its chunk plus `overhead` planes (the 2
+// halo planes and the start-up), a partial wave costing a whole one.  Chunks of
+// at least `min_len` planes (fewer chunks on a tie).
+inline int wave_chunk_length(int64_t N, int64_t blocks_per_chunk, int64_t slots, int64_t min_len,
+                             double overhead) {
+  double best = 1e300;
+  int64_t best_len = N;
+  for (int64_t gz = 1; gz <= std::max<int64_t>(1, N / min_len); ++gz) {
+    const int64_t len = (N + gz - 1) / gz, chunks = (N + len - 1) / len;
+    const int64_t waves = (blocks_per_chunk * chunks + slots - 1) / slots;
+    const double t = (double)waves * ((double)len + overhead);
+    if (t < best * (1.0 - 1e-9)) {
+      best = t;
+      best_len = len;
+    }
+  }
+  return (int)best_len;
+}
+
 }  // namespace plan
 }  // namespace ce

@@ -9,7 +9,12 @@ checked against the choices the GB300 timings fixed (CPU; no GPU needed):
   5.19 against 5.28 ms);
 * the row kernel's item length on one FP32 lattice (304 resident CTAs): the
   measured best among the item lengths timed (96^3: 4, 160^3: 16, 224^3: 48,
-  288^3: 96, 2D 2048^2: 16, 2D 16384^2: 128)."""
+  288^3: 96, 2D 2048^2: 16, 2D 16384^2: 128);
+* the chunk length of the column and line-sweep kernels (wave model, 3 blocks
+  per SM on 152 SMs): the plans their timings were taken with (383^3: 192 planes,
+  345.5 us, where the earlier "two waves of warps" rule took 77 planes, 406 us;
+  511^3: 73; 255^3: 29, 115.5 against 132.5 us at 37; 2D 6001^2: 172 rows), and
+  that every pick covers the axis with chunks of at least the minimum length."""
 import os
 import shutil
 import subprocess
@@ -30,6 +35,18 @@ int main() {
   // row kernel item length: dims, N (FP32: 4 sites per 16 bytes), 304 slots
   const int rl[][2] = {{3, 96}, {3, 160}, {3, 224}, {3, 288}, {2, 2048}, {2, 16384}, {1, 65536}};
   for (auto& c : rl) std::printf("r %d %d %d\n", c[0], c[1], rows_item_length(c[0], c[1], 4, 304));
+  // chunk length: N, blocks per chunk, minimum length (456 slots, 5 planes overhead)
+  const long long wc[][3] = {{383, 208, 4}, {511, 387, 4}, {255, 97, 4}, {6001, 26, 8}};
+  for (auto& c : wc) std::printf("w %lld %d\n", c[0], wave_chunk_length(c[0], c[1], 456, c[2], 5.0));
+  // invariants over a grid of cases: chunks of at least min(N, min_len), covering N
+  int bad = 0;
+  for (long long N = 3; N <= 700; N += 7)
+    for (long long b = 1; b <= 1000; b = b * 3 + 1)
+      for (long long m : {4LL, 8LL}) {
+        const long long len = wave_chunk_length(N, b, 456, m, 5.0), chunks = (N + len - 1) / len;
+        if (len < 1 || len > N || (len < m && len != N && N >= m) || chunks * len < N || (chunks - 1) * len >= N) ++bad;
+      }
+  std::printf("i %d\n", bad);
   return 0;
 }
 '''
@@ -45,22 +62,32 @@ def picks(tmp_path_factory):
     src.write_text(PROGRAM)
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
-    z, r = {}, {}
+    z, r, w, inv = {}, {}, {}, None
     for line in out.splitlines():
         f = line.split()
         if f[0] == "z":
             z[int(f[1])] = int(f[2])
-        else:
+        elif f[0] == "r":
             r[(int(f[1]), int(f[2]))] = int(f[3])
-    return z, r
+        elif f[0] == "w":
+            w[int(f[1])] = int(f[2])
+        else:
+            inv = int(f[1])
+    return z, r, w, inv
 
 
 def test_automatic_zchunks_match_the_measured_best(picks):
-    z, _ = picks
+    z = picks[0]
     assert z == {128: 19, 256: 4, 384: 6, 512: 8, 640: 12, 1024: 16}
 
 
 def test_row_kernel_item_length_matches_the_measured_best(picks):
-    _, r = picks
+    r = picks[1]
     assert r == {(3, 96): 4, (3, 160): 16, (3, 224): 48, (3, 288): 96, (2, 2048): 16, (2, 16384): 128,
                  (1, 65536): 128}
+
+
+def test_wave_chunk_length_picks_the_timed_plans(picks):
+    w, inv = picks[2], picks[3]
+    assert w == {383: 192, 511: 73, 255: 29, 6001: 172}
+    assert inv == 0
