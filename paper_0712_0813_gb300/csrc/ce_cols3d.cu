@@ -22,8 +22,9 @@
 // directions, so the two chunks that share a boundary read its planes at about
 // the same time.
 //
-// TY (rows per lane) keeps the registers per thread near 130: 8 rows for FP32
-// with up to 2 fields, 4 for more; FP64 8 / 4 / 2 rows for 1 / 2 / 3-4 fields.
+// TY (rows per lane), ColRows below: FP32 6 rows for 1-2 fields (4 below side
+// 160), 3 / 2 for 3 / 4 fields; FP64 4 rows for 1 field, 2 for more.  Loop
+// unrolled by 3 so that the three g buffers keep static register roles.
 #include <cstdint>
 
 #include "ce_device.cuh"
