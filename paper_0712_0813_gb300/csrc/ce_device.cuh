@@ -63,10 +63,9 @@ __device__ __forceinline__ void step1d_group(const T* const (&f_in)[4], const T*
                                              T* const (&f_out)[4], T* const (&w_out)[4], int64_t N, int64_t k,
                                              T c, T dd, T kk, T idx2, const T (&q)[3], T& g2loc, T& vloc) {
   constexpr int VX = 16 / sizeof(T);
-  const int64_t groups = N / VX;
   const int64_t s = k * VX;
   const int64_t sl = (k == 0) ? N - 1 : s - 1;             // left neighbour of the first site
-  const int64_t sr = (k == groups - 1) ? 0 : s + VX;       // right neighbour of the last site
+  const int64_t sr = (s + VX == N) ? 0 : s + VX;           // right neighbour of the last site
   T g[NF][VX + 2], v[NF][VX];   // g[i][1 + j] at site s + j; [0] and [VX + 1] the outer neighbours
 #pragma unroll
   for (int i = 0; i < NF; ++i) {

@@ -231,12 +231,46 @@ __global__ void __launch_bounds__(kGenericThreads) k_kick_from_g(const StepArgs<
   if (p.update_scalars) finish_step_block(p, grad2, pot);
 }
 
-// The 1D step for N a multiple of VX = 16 / sizeof(T): each thread takes
-// groups of VX consecutive sites (step1d_group: 16-byte loads and stores, the
-// outer neighbours by scalar loads that hit L1, each site's g formed once per
-// field).  Per site the arithmetic is that of k_step_generic (same operations
-// in the same order), so the fields agree bit for bit; the block sums are
-// added in another order.
+// One site s of a 1D lattice with the arithmetic of step1d_group (the sites
+// past the last whole 16-byte group of a side that is not a multiple of it).
+template <typename T, int NF>
+__device__ __forceinline__ void step1d_site(const T* const (&f_in)[4], const T* const (&w_in)[4],
+                                            T* const (&f_out)[4], T* const (&w_out)[4], int64_t N, int64_t s,
+                                            T c, T dd, T kk, T idx2, const T (&q)[3], T& g2loc, T& vloc) {
+  const int64_t sl = (s == 0) ? N - 1 : s - 1, sr = (s == N - 1) ? 0 : s + 1;
+  T gs[NF], v[NF], lap[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    const T f = __ldg(f_in[i] + s), fl = __ldg(f_in[i] + sl), fr = __ldg(f_in[i] + sr);
+    v[i] = fmaT(c, f, __ldg(w_in[i] + s));
+    const T gc = fmaT(dd, v[i], f);
+    const T gm = fmaT(dd, fmaT(c, fl, __ldg(w_in[i] + sl)), fl);
+    const T gp = fmaT(dd, fmaT(c, fr, __ldg(w_in[i] + sr)), fr);
+    T acc = T(0);
+    acc += (gp + gm) - T(2) * gc;
+    const T df = gp - gc;
+    g2loc = fmaT(df, df, g2loc);
+    lap[i] = acc * idx2;
+    gs[i] = gc;
+  }
+  T dv[NF], vs;
+  model_dv<T, NF>(gs, q, dv, vs);
+  vloc += vs;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    w_out[i][s] = fmaT(kk, lap[i] - dv[i], v[i]);
+    f_out[i][s] = gs[i];
+  }
+}
+
+// The 1D step for any N: each thread takes groups of VX = 16 / sizeof(T)
+// consecutive sites (step1d_group: 16-byte loads and stores, the outer
+// neighbours by scalar loads that hit L1, each site's g formed once per field;
+// the groups start at site 0, so every 16-byte access is aligned), and the
+// grid's last thread the N % VX sites after the last whole group
+// (step1d_site).  Per site the arithmetic is that of k_step_generic (same
+// operations in the same order), so the fields agree bit for bit; the block
+// sums are added in another order.
 template <typename T, int NF>
 __global__ void __launch_bounds__(kGenericThreads) k_step_1d(const StepArgs<T> p) {
   constexpr int VX = 16 / sizeof(T);
@@ -258,6 +292,10 @@ __global__ void __launch_bounds__(kGenericThreads) k_step_1d(const StepArgs<T> p
       since_flush = 0;
     }
   }
+  // the N % VX sites after the last whole group: the grid's last thread
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1)
+    for (int64_t s = groups * VX; s < N; ++s)
+      step1d_site<T, NF>(p.f_in, p.w_in, p.f_out, p.w_out, N, s, c, dd, kk, idx2, q, g2loc, vloc);
   if (p.update_scalars) finish_step_block(p, (double)g2acc + (double)g2loc, (double)vacc + (double)vloc);
 }
 
@@ -265,15 +303,12 @@ template <typename T, int NF>
 static cudaError_t launch_generic_nf(const StepArgs<T>& a, int blocks, cudaStream_t st) {
   constexpr int VX = 16 / sizeof(T);
   switch (a.dims) {
-    case 1:
-      if (a.N % VX == 0) {
-        const int64_t want = (a.N / VX + kGenericThreads - 1) / kGenericThreads;
-        const int b1 = (int)(want < blocks ? want : blocks);
-        k_step_1d<T, NF><<<b1 < 1 ? 1 : b1, kGenericThreads, 0, st>>>(a);
-      } else {
-        k_step_generic<T, NF, 1><<<blocks, kGenericThreads, 0, st>>>(a);
-      }
+    case 1: {
+      const int64_t want = (a.N / VX + kGenericThreads - 1) / kGenericThreads;
+      const int b1 = (int)(want < blocks ? want : blocks);
+      k_step_1d<T, NF><<<b1 < 1 ? 1 : b1, kGenericThreads, 0, st>>>(a);
       break;
+    }
     case 2: k_step_generic<T, NF, 2><<<blocks, kGenericThreads, 0, st>>>(a); break;
     default: k_step_generic<T, NF, 3><<<blocks, kGenericThreads, 0, st>>>(a); break;
   }

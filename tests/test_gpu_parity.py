@@ -55,6 +55,8 @@ CASES = [
     (3, 32, 20.0, 0.05, 2, (1.2,), True),
     (3, 64, 20.0, 0.02, 2, (1.2,), True),
     (1, 4096, 20.0, 0.004, 2, (1.2,), True),
+    (1, 4099, 20.0, 0.004, 2, (1.2,), True),  # 1D tail after the last 16-byte group
+    (1, 5, 3.0, 0.05, 1, (), True),
     (2, 256, 20.0, 0.02, 2, (1.2,), True),
     (3, 3, 2.0, 0.05, 2, (1.2,), True),      # every neighbour wraps
     (3, 5, 3.0, 0.05, 1, (), True),
@@ -552,3 +554,28 @@ def test_automatic_choice_2d_fp32(gpu_capi, N, expected):
     with gpu_capi.Simulation(dims=2, N=N, L=20.0, dt=courant_dt(2, N, 20.0, 1.0, (1.2,)), nfields=2, q=(1.2,),
                              precision="f32") as sim:
         assert sim.kernel == ids[expected] == auto_kernel(gpu_capi, 2, N, "f32")
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("N", [3, 5, 7, 4097, 4099])
+def test_1d_ragged_shift_invariance(gpu_capi, N, precision):
+    """1D sides that are not a multiple of the 16-byte group (4 sites in FP32,
+    2 in FP64): the sites after the last whole group take the one-site path,
+    the others the grouped one, with the same per-site arithmetic.  Without
+    expansion (no global sums feed back) a periodic shift of the initial state
+    then shifts the result bit for bit after 20 steps, whichever sites fall in
+    the tail (sides below one group are all tail)."""
+    L, q = 3.0 if N < 10 else 20.0, (1.2,)
+    f0, u0 = lattice_ics(1, N, L, 2, q=q, seed=6, amp=1e-2)
+    f0, u0 = np.asarray(f0).reshape(2, N), np.asarray(u0).reshape(2, N)
+    dt = courant_dt(1, N, L, 1.0, q)
+    out = []
+    for shift in (0, 1):
+        with gpu_capi.Simulation(dims=1, N=N, L=L, dt=dt, nfields=2, q=q, expansion=False,
+                                 precision=precision) as sim:
+            sim.set_fields(np.roll(f0, shift, axis=-1), np.roll(u0, shift, axis=-1))
+            sim.step(20)
+            f, v, _ = sim.get_fields(gpu_capi.CE_VEL_STAGGERED)
+            out.append((np.asarray(f).reshape(2, N), np.asarray(v).reshape(2, N)))
+    (f, v), (fs, vs) = out
+    assert np.array_equal(np.roll(f, 1, axis=-1), fs) and np.array_equal(np.roll(v, 1, axis=-1), vs), N
