@@ -23,7 +23,8 @@ fields, dt = 0.02 (plan 8 rows / 4 stages / 4 z-chunks); 3D 512^3, 4 fields,
 q = (0.8, 5, 40) (plan 8 / 5 / 8); 3D 1024^3, 2 fields (the automatic plan,
 then 16 / 4 / 8 on the same state); all FP32 storage with expansion; and the
 96-lattice mixed batch (FP32, batched kernel, the item length the bench's
-autotuner picks).  Tolerances: f and v
+autotuner picks); and the odd sides 511^3 (column kernel) and 16001^2 (line-sweep
+kernel) on the automatic choice.  Tolerances: f and v
 within an error bound of one FP32 step derived from the arithmetic
 (`check_one_step`; on the finest lattices the Laplacian's 1/dx^2 weights make
 the FP32 rounding of g the dominant term), a(t) to 1e-12, and a', a'' to 1e-5
@@ -121,6 +122,60 @@ def test_full_size_sampled_step(gpu_capi, orc, name, N, nf, q, dt, plans):
             after = sim.sample_fields(sites)
             check_one_step(orc, local, p, before, after, sites, stencil, G, V)
             assert after[2].step == 4 + k
+
+
+# The column kernel (3D) and the line-sweep kernel (2D) at the largest odd sides
+# timed in the profiles, on the automatic choice: 30-site strips in x, 6-row
+# groups in 3D, chunks along the sweep axis (z in 3D, y in 2D) of the length the
+# wave model picks on GB300 (511^3: 73 planes; 16001^2: 471 rows), FP32 storage
+# with expansion.
+ODD = [("511cube", 3, 511, 73), ("16001sq", 2, 16001, 471)]
+
+
+def odd_sites(dims, N, chunk, n_random=20000, seed=12):
+    """Random sites plus every combination of strip edges, row-group edges,
+    chunk boundaries along the sweep axis and lattice edges."""
+    last = 30 * ((N - 1) // 30)
+    xs = {0, 1, 29, 30, 31, 59, 60, N // 2, last - 1, last, last + 1, N - 2, N - 1}
+    sweep = {0, 1, N // 2, N - 2, N - 1}
+    for k in range(1, (N + chunk - 1) // chunk):
+        sweep |= {k * chunk - 1, k * chunk, k * chunk + 1}
+    if dims == 3:
+        ys = {0, 1, 5, 6, 7, 11, 12, N // 2, N - 7, N - 6, N - 2, N - 1}
+        axes = [sorted(x for x in xs if x < N), sorted(y for y in ys if y < N), sorted(z for z in sweep if z < N)]
+    else:
+        axes = [sorted(x for x in xs if x < N), sorted(y for y in sweep if y < N)]
+    grid = np.meshgrid(*[np.array(a, dtype=np.int64) for a in axes], indexing="ij")
+    edges = sum(g * N ** d for d, g in enumerate(grid)).reshape(-1)
+    rng = np.random.default_rng(seed)
+    rand = rng.integers(0, N ** dims, size=n_random)
+    return np.unique(np.concatenate([edges, rand]).astype(np.int64))
+
+
+@pytest.mark.parametrize("name,dims,N,chunk", ODD, ids=[c[0] for c in ODD])
+def test_full_size_odd_side_sampled_step(gpu_capi, orc, name, dims, N, chunk):
+    import torch
+    from oracle import local
+    capi = gpu_capi
+    L, nf, q = 20.0, 2, (1.2,)
+    dt = courant_dt(dims, N, L, 1.0, q)
+    p = orc.Params(dims=dims, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
+    f0, u0 = lattice_ics(dims, N, L, nf, q=q, seed=1, backend="torch")
+    torch.cuda.empty_cache()
+    with capi.Simulation(dims=dims, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision="f32") as sim:
+        assert sim.kernel == capi.CE_KERNEL_PLANES
+        sim.set_fields(f0, u0)
+        del f0, u0
+        gc.collect()
+        sim.step(3)
+        sites = odd_sites(dims, N, chunk)
+        stencil = local.stencil_sites(dims, N, sites)
+        before = sim.sample_fields(stencil)
+        G, V = oracle_sums(local, p, sim)
+        sim.step(1)
+        after = sim.sample_fields(sites)
+        check_one_step(orc, local, p, before, after, sites, stencil, G, V)
+        assert after[2].step == 4
 
 
 def test_mixed_batch_sampled_step(gpu_capi, orc):
