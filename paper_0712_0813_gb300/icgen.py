@@ -37,14 +37,16 @@ def mode_grid(dims: int, N: int) -> np.ndarray:
 
 def lattice_ics(dims: int, N: int, L: float, nf: int, phi0: float = 1.0,
                 q=(1.2,), amp: float = 1e-4, seed: int = 1,
-                kcut_frac: float = 0.25, backend: str = "numpy"):
+                kcut_frac: float = 0.25, backend: str = "numpy", pinned: bool = False):
     """Return (f, u) as float64 arrays of shape (nf, N**dims), layout [field][z][y][x].
 
     backend "numpy" transforms on the host; "torch" draws the same phases and
     runs the inverse FFT with torch (on the GPU when one is present), which is
-    what large lattices (512^3 and up) need."""
+    what large lattices (512^3 and up) need.  pinned (torch backend with a GPU):
+    the arrays live in page-locked host memory, so host<->device copies from and
+    into them need no staging."""
     if backend == "torch":
-        return _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac)
+        return _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac, pinned)
     shape = (N,) * dims
     S = N ** dims
     n2 = mode_grid(dims, N)
@@ -68,7 +70,7 @@ def lattice_ics(dims: int, N: int, L: float, nf: int, phi0: float = 1.0,
     return f, u
 
 
-def _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac):
+def _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac, pinned=False):
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     shape = (N,) * dims
@@ -76,8 +78,12 @@ def _lattice_ics_torch(dims, N, L, nf, phi0, q, amp, seed, kcut_frac):
     n2 = torch.as_tensor(mode_grid(dims, N), device=dev)
     k = 2.0 * math.pi * torch.sqrt(n2) / L
     keep = (n2 > 0) & (torch.sqrt(n2) <= kcut_frac * N)
-    f = np.empty((nf, S))
-    u = np.empty((nf, S))
+    if pinned and dev == "cuda":
+        f = torch.empty((nf, S), dtype=torch.float64, pin_memory=True).numpy()
+        u = torch.empty((nf, S), dtype=torch.float64, pin_memory=True).numpy()
+    else:
+        f = np.empty((nf, S))
+        u = np.empty((nf, S))
     qs = list(q) + [0.0] * 4
     scale = amp * math.sqrt(S)
     for i in range(nf):
