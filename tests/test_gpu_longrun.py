@@ -42,7 +42,7 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "longrun_256cube.json")
 STAT_TOL = {"f64": 1e-8, "f32": 1e-3}
 EPS32 = 2.0 ** -24
-# relative max error after 100 steps: FP64 the benchmark spec's 1e-11; FP32 storage
+# relative max error after 100 steps: FP64 the 1e-11 of the FP64 parity tests; FP32 storage
 # against the FP64 oracle, the 32^3 FP32 parity test's bounds (f 1e-5, v 1e-3)
 POINT_TOL = {"f64": (1e-11, 1e-11), "f32": (1e-5, 1e-3)}
 
