@@ -152,8 +152,12 @@ def odd_sites(dims, N, chunk, n_random=20000, seed=12):
     return np.unique(np.concatenate([edges, rand]).astype(np.int64))
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("name,dims,N,chunk", ODD, ids=[c[0] for c in ODD])
-def test_full_size_odd_side_sampled_step(gpu_capi, orc, name, dims, N, chunk):
+def test_full_size_odd_side_sampled_step(gpu_capi, orc, name, dims, N, chunk, precision):
+    """FP32: the column / line-sweep kernel (the automatic choice); FP64: the
+    automatic FP64 choice on the same lattice (the generic kernel's two passes),
+    within FP64 bounds of one step and a'' to 1e-10 of its source term."""
     import torch
     from oracle import local
     capi = gpu_capi
@@ -162,8 +166,8 @@ def test_full_size_odd_side_sampled_step(gpu_capi, orc, name, dims, N, chunk):
     p = orc.Params(dims=dims, N=N, L=L, dt=dt, nf=nf, q=q, expansion=True)
     f0, u0 = lattice_ics(dims, N, L, nf, q=q, seed=1, backend="torch")
     torch.cuda.empty_cache()
-    with capi.Simulation(dims=dims, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision="f32") as sim:
-        assert sim.kernel == capi.CE_KERNEL_PLANES
+    with capi.Simulation(dims=dims, N=N, L=L, dt=dt, nfields=nf, q=q, expansion=True, precision=precision) as sim:
+        assert sim.kernel == (capi.CE_KERNEL_PLANES if precision == "f32" else capi.CE_KERNEL_GENERIC)
         sim.set_fields(f0, u0)
         del f0, u0
         gc.collect()
@@ -174,7 +178,10 @@ def test_full_size_odd_side_sampled_step(gpu_capi, orc, name, dims, N, chunk):
         G, V = oracle_sums(local, p, sim)
         sim.step(1)
         after = sim.sample_fields(sites)
-        check_one_step(orc, local, p, before, after, sites, stencil, G, V)
+        if precision == "f32":
+            check_one_step(orc, local, p, before, after, sites, stencil, G, V)
+        else:
+            check_one_step(orc, local, p, before, after, sites, stencil, G, V, eps=EPS64, sums_rel=1e-10)
         assert after[2].step == 4
 
 
