@@ -91,15 +91,15 @@ def kernel_source_hash(kernel_name: str) -> str:
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel_name: str, precision: str, sites: int):
+def ncu_traffic(kernel_name: str, precision: str, sites: int, nf: int):
     """DRAM bytes per launch from the committed ncu record, if it was taken on
-    the current kernel source (same hash), scaled from the captured lattice's
-    sites to `sites` (the traffic of the streaming kernel grows with the sites
-    it processes); else None.  Returns (bytes, note)."""
+    the current kernel source (same hash) with the same field count, scaled
+    from the captured lattice's sites to `sites` (the traffic of the streaming
+    kernel grows with the sites it processes); else None.  Returns (bytes, note)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.md")
     if not os.path.exists(path):
         return None, None
-    pat = re.compile(rf"^traffic\s+{re.escape(kernel_name)}\s+{precision}\s+src=(\w+)\s+"
+    pat = re.compile(rf"^traffic\s+{re.escape(kernel_name)}\s+{precision}\s+nf={nf}\s+src=(\w+)\s+"
                      rf"bytes_per_launch=(\d+)\s+sites=(\d+)")
     cur = kernel_source_hash(kernel_name)
     with open(path) as fh:
@@ -294,7 +294,7 @@ def roofline_of(w, precision, ms_per_step, hbm_peak, peak_kind, kernel):
     achieved = alg / (ms_per_step / 1e3) / 1e9
     kname = {"sweep": "k_step_sweep", "rows": "k_step_batched",
              "planes": "k_step_cols" if w["dims"] == 3 else "k_step_lines"}.get(kernel, "k_step_generic")
-    traffic, note = ncu_traffic(kname, precision, S) if kname in STEP_SOURCES else (None, None)
+    traffic, note = ncu_traffic(kname, precision, S, w["nf"]) if kname in STEP_SOURCES else (None, None)
     out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
            "traffic": traffic, "kernel": kname, "algorithmic_bytes_per_launch": alg, "peak_kind": peak_kind}
     if note:
