@@ -755,8 +755,8 @@ def main():
     if args.plan:
         r_, s_, z_ = (int(x) for x in args.plan.split(","))
         hints = {"tile_rows": r_, "stages": s_, "zchunks": z_}
-    elif not args.no_autotune and w["dims"] == 3:
-        tune = True
+    elif not args.no_autotune and w["dims"] == 3 and args.precision == "f32":
+        tune = True   # (FP64 keeps the automatic choice: the generic kernel's two passes, faster in FP64)
     ms, kernel, clocks, plan, tune_info = time_device_steps(
         capi, torch, w, f0, u0, args.precision, args.steps, args.warmup, barrier,
         sampler_gpu=gpu_index if rank == 0 else None, hints=hints, tune=tune)
@@ -768,6 +768,8 @@ def main():
     secs = ms / 1e3
     value = replicas.aggregate_throughput(ws, S * args.steps, secs) / 1e9
     roofline = roofline_of(w, args.precision, ms / args.steps, hbm_peak, peak_kind, kernel)
+    if args.precision == "f64":   # bound by the FP64 pipe, not by HBM: that roofline when it is known
+        roofline = fp64_alu_roofline(w, value / ws, kernel, hbm_peak) or roofline   # per GPU
 
     # plain FP64 path on the same lattice: the library's automatic FP64 choice
     w64 = min(args.warmup, 5)
@@ -838,7 +840,7 @@ def main():
                        "l2": f"state {4 * esize * w['nf'] * S / 1e6:.0f} MB > L2 (129 MB); no flush needed"},
             "fp64_plain": {"value": value64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                            "kernel": kernel64, "sweep_plan": list(plan64), "f32_over_f64": value / value64,
-                           "roofline": fp64_alu_roofline(w, value64, kernel64, hbm_peak)},
+                           "roofline": fp64_alu_roofline(w, value64 / ws, kernel64, hbm_peak)},
             "roofline": roofline,
             "fp32_vs_fp64": fp32_vs_fp64,
             "cube256": cube256,
